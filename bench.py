@@ -1,0 +1,343 @@
+"""Benchmark of the GB300 LBGK library: MLUPS and HBM-roofline fraction of the fused step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Workloads (synthetic, shaped like the paper's cases):
+  beam1024x1  the tau*omega = 1 instance of beam1024 alone (profiling).
+  beam1024  D2Q37, 4th-order equilibrium, regularized collision, FP32 storage: a 32 x 32 beam
+            section centred in a 1024^2 periodic box, body-frame drive, three instances at
+            tau*omega = 0.01, 1, 10 (default).  One bench step advances every instance by one
+            lattice step (one fused kernel launch each).
+  plate9    D2Q9 plain BGK, FP64: the 4 x 256 oscillating plate (latency-bound correctness case).
+  beam2048-<f32|f16|bf16|f64>  D2Q37-H4 beam in a 2048^2 box, tau*omega = 0.1, 1, 10.
+
+Each rank (torchrun, one per GPU) runs its own replicas: the instances are independent, so the
+work is sharded with no collective on the data path (weak scaling).  One JSON line is printed by
+rank 0.  `--impl reference` times the FP64 CPU oracle on the host cores for the same workload and
+metric on a bounded sample (whole lattice, a few steps).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STORE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
+
+
+def workload_list(name):
+    from paper_0904_4504_gb300 import inputs as I
+    if name == "beam1024":
+        return [I.beam_d2q37_h4(to) for to in I.BEAM_TAU_OMEGAS]
+    if name == "beam1024x1":
+        return [I.beam_d2q37_h4(1.0)]
+    if name == "plate9":
+        return [I.plate_d2q9_fp64()]
+    if name.startswith("beam2048-"):
+        st = STORE[name.split("-")[1]]
+        return [I.beam_d2q37_h4(to, n=2048, storage=st) for to in I.PRECISION_TAU_OMEGAS]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def create(L, w, orc_params):
+    tau, omega = orc_params(w)
+    geom = L.make_geometry(kind=w.geometry, lx=w.lx, ly=w.ly, drive=w.drive, u0=w.u0, eq_order=w.eq_order,
+                           collision=w.collision, storage=w.storage)
+    return L.lbm_create(w.lattice, w.nx, w.ny, tau, omega, geom)
+
+
+def lattice_params(L):
+    def f(w):
+        if w.tau is not None:
+            return w.tau, w.omega
+        tau, omega, _ = L.lbm_params_from_tau_omega(w.lattice, w.tau_omega)
+        return tau, omega
+    return f
+
+
+def run_ours(args):
+    import torch
+    from paper_0904_4504_gb300 import lbm as L
+    from paper_0904_4504_gb300.builder import build
+
+    rank, world, local = dist_setup(args.gpus)
+    build()
+    wl = workload_list(args.workload)
+    params = lattice_params(L)
+    stream = torch.cuda.Stream()
+    sims = []
+    for w in wl:
+        h = create(L, w, params)
+        L.lbm_set_stream(h, stream)
+        if args.tile:
+            L.lbm_set_tile(h, *args.tile)
+        sims.append(h)
+    infos = [L.lbm_info(h) for h in sims]
+    fluid = sum(i["n_fluid"] for i in infos)
+    bytes_step = sum(i["bytes_per_step"] for i in infos)
+
+    for _ in range(args.warmup):
+        for h in sims:
+            L.lbm_step(h, 1)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            for h in sims:
+                L.lbm_step(h, 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    for h in sims:
+        L.lbm_synchronize(h)
+    launches = args.steps * len(sims)
+    value = fluid * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # dominant kernel: the fused step (one launch per instance per step)
+    peak, peak_kind = peaks()
+    per_launch_s = ms * 1e-3 / launches
+    achieved = bytes_step / len(sims) / per_launch_s / 1e9
+
+    # end to end through the C ABI: create (geometry upload) -> K steps -> force history (D2H) -> fit
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for w in wl:
+            h = create(L, w, params)
+            L.lbm_step(h, args.steps)
+            F = L.lbm_force_history(h)
+            d2h += F.nbytes
+            h2d += L.lbm_info(h)["h2d_bytes"]
+            L.lbm_destroy(h)
+        t1 = time.perf_counter()
+        e2e_s = max_over_ranks(t1 - t0, world)
+        e2e = {"value": fluid * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "scope": "lbm_create (host geometry + upload) -> lbm_step(K) -> lbm_force_history"}
+    for h in sims:
+        L.lbm_destroy(h)
+
+    cpu = cpu_baseline(wl, params, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if rank == 0:
+        w0 = wl[0]
+        line = {
+            "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction of the fused step",
+            "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE_NAME[w0.storage], "data": "synthetic",
+            "config": {"workload": args.workload, "instances": [w.name for w in wl], "lattice": f"D2Q{w0.lattice}",
+                       "eq_order": w0.eq_order, "collision": "regularized" if w0.collision == 1 else "bgk",
+                       "nodes_per_instance": [w.nx * w.ny for w in wl], "fluid_nodes": fluid,
+                       "l2": "inputs larger than L2 (no flush)" if bytes_step / len(wl) > 2 * 129e6 else
+                             "inputs smaller than L2", "parallelism": f"replicas x{world}",
+                       "tile": list(args.tile) if args.tile else [infos[0]["block_x"], infos[0]["block_y"]]},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": "step_kernel (fused stream+collide+force)",
+                         "bytes_per_launch": bytes_step // len(wl)},
+            "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, params, args, budget_s=15.0):
+    """The FP64 oracle on the host cores: whole-lattice steps of the first instance until about
+    budget_s of CPU work."""
+    import oracle as orc
+    w = wl[0]
+    tau, omega = params(w)
+    lab = {0: lambda: orc.geometry_plate(w.lattice, w.nx, w.ny), 1: lambda: orc.geometry_beam(w.nx, w.ny, w.lx, w.ly)}[
+        w.geometry]()
+    nt = orc.max_threads()
+    f = orc.rest_state(w.lattice, w.nx, w.ny)
+    steps, t_used = 0, 0.0
+    while t_used < budget_s and steps < 10000:
+        n = 1 if w.nx * w.ny > 1e5 else 200
+        t0 = time.perf_counter()
+        f, _ = orc.run(w.lattice, lab, tau, omega, w.u0, n, eq_order=w.eq_order, collision=w.collision, drive=w.drive,
+                       f=f, n0=steps, nthreads=nt)
+        t_used += time.perf_counter() - t0
+        steps += n
+    fluid = int((lab == 0).sum())
+    return {"value": round(fluid * steps / t_used / 1e6, 4), "unit": "MLUPS", "cores": nt, "kind": "oracle",
+            "sample": f"{steps} whole-lattice steps of {w.name} ({fluid} fluid nodes), FP64, {nt} OpenMP threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload_list(args.workload)
+    import oracle as orc
+
+    def params(w):
+        if w.tau is not None:
+            return w.tau, w.omega
+        t, o, _ = orc.params_from_tau_omega(w.lattice, w.tau_omega)
+        return t, o
+
+    orc.build()
+    nt = orc.max_threads()
+    labs = [{0: lambda w=w: orc.geometry_plate(w.lattice, w.nx, w.ny),
+             1: lambda w=w: orc.geometry_beam(w.nx, w.ny, w.lx, w.ly)}[w.geometry]() for w in wl]
+    states = [orc.rest_state(w.lattice, w.nx, w.ny) for w in wl]
+    fluid = [int((lab == 0).sum()) for lab in labs]
+
+    def one(step_idx):
+        k = step_idx % len(wl)
+        w = wl[k]
+        tau, omega = params(w)
+        states[k], _ = orc.run(w.lattice, labs[k], tau, omega, w.u0, 1, eq_order=w.eq_order, collision=w.collision,
+                               drive=w.drive, f=states[k], n0=step_idx // len(wl), nthreads=nt)
+        return fluid[k]
+
+    for s in range(args.warmup):
+        one(s)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        done += one(args.warmup + s)
+    dt = time.perf_counter() - t0
+    v = done / dt / 1e6
+    w0 = wl[0]
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction "
+                                       "of the fused step",
+        "value": round(v, 4), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": [w.name for w in wl], "lattice": f"D2Q{w0.lattice}"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": nt, "kind": "oracle",
+                         "sample": f"one whole-lattice step of one instance per bench step (instances in turn), "
+                                   f"FP64 oracle, {nt} OpenMP threads"},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="beam1024")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann-BGK library (liblbm.so).
+ *
+ * The library runs the time step of the LBGK method of Colosqui, Karabacak, Ekinci & Yakhot,
+ * "Lattice Boltzmann simulation of high-frequency flows: electromechanical resonators in gaseous
+ * media" (2009), Sec. 5: advection (Eq. 17), moments (Eq. 16), Hermite equilibrium (Eq. 15),
+ * regularized BGK collision (Eqs. 18-19), with bounce-back walls (Eq. 12) that move with
+ * U_w = u0 sin(omega t) x (Sec. 6, "Fluid-solid interaction") or, in the body frame, a uniform
+ * body force rho u0 omega cos(omega t) x on the fluid.  Each step also records the force on the body
+ * by momentum exchange, in FP64; fitting it to sin/cos gives the dissipative and inertial parts of
+ * the fluid force F_f of Eq. 1 and the normalized damping of Eq. 20.
+ *
+ * Units and conventions (all calls).
+ *   - Lattice units: dx = dt = 1, lattice speed 1.  theta = c_s^2 = 1/1.19697977039307^2 for D2Q37
+ *     (Appendix A, Table "D2Q37"), 1/3 for D2Q9 (textbook lattice, not in the paper).
+ *   - tau is the LBGK relaxation time in steps (tau > 1/2); the physical nondimensional frequency
+ *     of Sec. 6 is (tau - 1/2) * omega, because nu = theta (tau - 1/2) and tau_phys = nu / theta.
+ *   - The wall velocity and body force of step n -> n+1 are taken at t = n + 1/2; the force of
+ *     step n is stamped at the same time.
+ *   - Grids are periodic in x and y.  Walls are solid nodes inside the box (labels, below).
+ *   - Direction order: index 0 is the rest velocity; (1 + 2k, 2 + 2k) are +c and -c of pair k.
+ *     lbm_lattice_velocities() returns the table.
+ *   - Every call returns 0 on success or a negative LBM_E* code; lbm_last_error() then holds a
+ *     message for the calling thread.  No call aborts the process.
+ *   - All device memory of a simulation is allocated by lbm_create() and freed by lbm_destroy().
+ *     Host buffers passed in are owned by the caller and are not kept after the call returns.
+ *   - A simulation is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* bad argument: tau <= 1/2, u0 >= omega, grid too small, ...     */
+#define LBM_ENOMEM (-2)      /* device or host allocation failed                                 */
+#define LBM_ECUDA (-3)       /* a CUDA call failed (message in lbm_last_error)                   */
+#define LBM_ETIMEOUT (-4)    /* a bounded device wait gave up                                    */
+#define LBM_ENONFINITE (-5)  /* the force became NaN or Inf: the run diverged                    */
+#define LBM_ERANGE (-6)      /* index or size out of range                                       */
+
+typedef struct lbm_sim lbm_sim; /* opaque; owned by the library */
+
+enum { LBM_D2Q9 = 9, LBM_D2Q37 = 37 };
+enum { LBM_GEOM_PLATE = 0, LBM_GEOM_BEAM = 1, LBM_GEOM_MASK = 2, LBM_GEOM_NONE = 3 };
+enum { LBM_DRIVE_WALL = 0, LBM_DRIVE_BODYFORCE = 1 };
+enum { LBM_COLL_BGK = 0, LBM_COLL_REGULARIZED = 1 };
+enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16 = 3 };
+
+/* Node labels of a geometry (LBM_GEOM_MASK input, lbm_get_labels output). */
+enum { LBM_FLUID = 0, LBM_BODY = 1, LBM_WALL = 2 };
+
+typedef struct {
+    int kind;                  /* LBM_GEOM_*                                                       */
+    int lx, ly;                /* BEAM: section lx nodes along the motion (x), ly across (y),
+                                  centred in the box, AR = ly/lx (Sec. 3).  Others: ignored.        */
+    int drive;                 /* LBM_DRIVE_WALL: label-1 nodes move with U_w = u0 sin(omega t) x;
+                                  LBM_DRIVE_BODYFORCE: body frame, fluid force rho u0 omega
+                                  cos(omega t) x, all walls static.                                 */
+    double u0;                 /* drive amplitude, 0 <= u0 < omega (Sec. 6: U_0 < omega dx)        */
+    double rho0;               /* rest density (> 0; 1 if 0 is passed)                            */
+    const unsigned char* mask; /* MASK: ny*nx row-major labels (0 fluid, 1 body, 2 static wall),
+                                  copied; solids must be at least the lattice reach (1 for D2Q9,
+                                  3 for D2Q37) thick, or links tunnel through them                 */
+    int eq_order;              /* 2 (Eq. 15) or 4 (Hermite continuation); D2Q9 requires 2         */
+    int collision;             /* LBM_COLL_REGULARIZED (Eqs. 18-19) or LBM_COLL_BGK (Eq. 14)      */
+    int storage;               /* LBM_STORE_*: population storage type; arithmetic is FP64 for F64
+                                  and FP32 otherwise; the force is accumulated in FP64              */
+} lbm_geometry;
+
+/*
+ * Create a simulation on the current CUDA device: nx * ny nodes of lattice Q (LBM_D2Q9 or
+ * LBM_D2Q37), relaxation time tau, drive angular frequency omega (rad/step), geometry `geom`.
+ * PLATE: the bottom R rows are the plate (label 1), the top R rows a static wall (label 2), R the
+ * lattice reach.  BEAM: an lx x ly body.  NONE: a periodic box with no solid.  The fluid starts at
+ * rest, f_i = w_i rho0 (step 0).  Requires nx, ny >= 2R + 1.  *out receives the handle.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_geometry* geom, lbm_sim** out);
+
+/* Enqueue n >= 0 time steps on the simulation's stream (asynchronous: returns before they run). */
+int lbm_step(lbm_sim* sim, long n);
+
+/* Wait for all enqueued steps; reports LBM_ENONFINITE if the force has become NaN/Inf. */
+int lbm_synchronize(lbm_sim* sim);
+
+/*
+ * Copy the force history to host memory: out_xy[2k], out_xy[2k+1] = (Fx, Fy) on the body (label 1)
+ * during step k, FP64, for k < min(cap_steps, steps done).  *n_steps receives the number of steps
+ * done.  Synchronizes the stream first.
+ */
+int lbm_force_history(lbm_sim* sim, double* out_xy, size_t cap_steps, size_t* n_steps);
+
+/*
+ * Least-squares fit Fx(t_n) = A sin(omega t_n) + B cos(omega t_n) + C over the steps after the
+ * first `skip_periods` periods (t_n = n + 1/2).  The body velocity is V(t) = s u0 sin(omega t) with
+ * s = +1 for the wall drive and s = -1 in the body frame (where the fluid force equals -dV/dt), so
+ * f_in = s A is the force part in phase with V (the dissipative part of F_f in Eq. 1) and
+ * f_q = s B the part in phase with dV/dt (inertial); f_0 = C.  Any output pointer may be NULL.
+ * Errors: LBM_ERANGE if fewer than one period remains after the skip.
+ */
+int lbm_fit(lbm_sim* sim, double skip_periods, double* f_in, double* f_q, double* f_0);
+
+/* Normalized damping of Eq. 20 per unit length: -f_in / (u0 rho0 sqrt(theta/2) perimeter). */
+int lbm_gamma_bar(lbm_sim* sim, double f_in, double perimeter, double* gamma_bar);
+
+/* Free all memory of the simulation (waits for its work).  NULL is allowed. */
+void lbm_destroy(lbm_sim* sim);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* Run the simulation's work on `stream` (a cudaStream_t owned by the caller, who keeps it alive
+ * until lbm_destroy or the next lbm_set_stream; 0 is the CUDA default stream).  Work already
+ * enqueued is completed first.  Until this is called the simulation uses a private stream. */
+int lbm_set_stream(lbm_sim* sim, void* stream);
+
+/*
+ * Deviations g_i = f_i - w_i rho0 of the current post-collision state, FP64, as count = Q*ny*nx
+ * values in [Q][ny][nx] order (direction order of lbm_lattice_velocities).  Synchronizes.
+ */
+int lbm_get_state(lbm_sim* sim, double* out, size_t count);
+
+/* Overwrite the current state with deviations g (same layout as lbm_get_state), rounded to the
+ * storage type.  Values at solid nodes are ignored (solid nodes hold g = 0). */
+int lbm_set_state(lbm_sim* sim, const double* g, size_t count);
+
+/* Node labels (ny*nx, row-major) the simulation runs with. */
+int lbm_get_labels(lbm_sim* sim, unsigned char* out, size_t count);
+
+typedef struct {
+    int lattice, nx, ny, pitch;  /* pitch: elements per stored row                               */
+    int storage, collision, eq_order, drive;
+    double tau, omega, u0, rho0, theta;
+    long steps_done;
+    size_t n_fluid, n_boundary;  /* fluid nodes; fluid nodes with at least one blocked link     */
+    size_t bytes_per_step;       /* algorithmic HBM bytes of one step: 2 Q sizeof(storage) n_fluid */
+    size_t device_bytes;         /* device memory held by the simulation                          */
+    int block_x, block_y;        /* tile shape of the step kernel                                  */
+    size_t h2d_bytes, d2h_bytes; /* host<->device bytes copied by the library so far               */
+} lbm_info_t;
+
+int lbm_info(lbm_sim* sim, lbm_info_t* out);
+
+/* Set the step kernel's tile (block_x a multiple of 32, block_x * block_y <= 512). */
+int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
+
+/* Velocity table of a lattice in the library's direction order: c_xy[2i], c_xy[2i+1], w[i], theta.
+ * Any output may be NULL.  Returns Q, or LBM_EINVAL. */
+int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta);
+
+/*
+ * Lattice parameters for a nondimensional frequency tau_omega = (tau - 1/2) omega (Sec. 6:
+ * tau = mu/p = nu/theta): the period is P = max(p_min, ceil(2 pi delta_min / sqrt(2 theta
+ * tau_omega))) steps, which puts delta_min nodes in the Stokes layer sqrt(2 nu/omega); then
+ * omega = 2 pi / P and tau = 1/2 + tau_omega / omega.  Outputs may be NULL.
+ */
+int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, int p_min, double* tau,
+                              double* omega, int* period);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,756 @@
+// capi.cu -- host runtime and C ABI of liblbm.so (declarations and contracts in include/lbm.h).
+//
+// The runtime rasterizes the geometry, classifies nodes and blocked links once, owns the device
+// buffers of a simulation, tabulates the drive in FP64, launches the fused step kernel once per
+// time step on the simulation's stream, and reads back the FP64 force history.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "runtime.h"
+#include "step_kernel.cuh"
+
+namespace lbm {
+
+void* find_launcher_q9(int storage, int coll, bool batched);
+void* find_launcher_q37_wide(int storage, int coll, bool batched);
+void* find_launcher_q37_half(int storage, int coll, bool batched);
+
+static void* find_launcher(int Q, int storage, int coll, bool batched) {
+    if (Q == 9) return find_launcher_q9(storage, coll, batched);
+    if (Q == 37) return storage <= ST_F32 ? find_launcher_q37_wide(storage, coll, batched)
+                                          : find_launcher_q37_half(storage, coll, batched);
+    return nullptr;
+}
+
+StepLaunchFn find_step_launcher(int Q, int storage, int coll) {
+    return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
+}
+BatchLaunchFn find_batch_launcher(int Q, int storage, int coll) {
+    return reinterpret_cast<BatchLaunchFn>(find_launcher(Q, storage, coll, true));
+}
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+const char* last_error() { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------------------------
+// lattice tables on the host (same constants as the device, lattice.cuh)
+// ---------------------------------------------------------------------------------------------
+
+template <class L>
+static void fill_lattice(HostLattice& H) {
+    H.Q = L::Q;
+    H.R = L::R;
+    H.theta = L::theta();
+    for (int i = 0; i < L::Q; ++i) {
+        H.c[i][0] = cx_of<L>(i);
+        H.c[i][1] = cy_of<L>(i);
+        H.w[i] = w_of<L>(i);
+        H.opp[i] = opp_of<L>(i);
+    }
+}
+
+bool host_lattice(int Q, HostLattice& H) {
+    if (Q == 9) { fill_lattice<D2Q9>(H); return true; }
+    if (Q == 37) { fill_lattice<D2Q37>(H); return true; }
+    return false;
+}
+
+size_t storage_size(int storage) {
+    switch (storage) {
+        case ST_F64: return 8;
+        case ST_F32: return 4;
+        case ST_BF16:
+        case ST_F16: return 2;
+        default: return 0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// geometry: labels, node classes and blocked links
+// ---------------------------------------------------------------------------------------------
+
+int build_labels(int Q, int nx, int ny, const lbm_geometry& g, std::vector<uint8_t>& lab) {
+    HostLattice H;
+    host_lattice(Q, H);
+    lab.assign((size_t)nx * ny, 0);
+    switch (g.kind) {
+        case LBM_GEOM_NONE:
+            break;
+        case LBM_GEOM_PLATE:
+            if (ny < 2 * H.R + 1) return set_error(LBM_EINVAL, "plate needs ny >= %d", 2 * H.R + 1);
+            for (int y = 0; y < H.R; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    lab[(size_t)y * nx + x] = LBM_BODY;
+                    lab[(size_t)(ny - 1 - y) * nx + x] = LBM_WALL;
+                }
+            break;
+        case LBM_GEOM_BEAM: {
+            if (g.lx < 1 || g.ly < 1 || g.lx > nx - 2 * H.R || g.ly > ny - 2 * H.R)
+                return set_error(LBM_EINVAL, "beam %dx%d does not fit a %dx%d box with a %d-node gap", g.lx, g.ly,
+                                 nx, ny, H.R);
+            const int x0 = (nx - g.lx) / 2, y0 = (ny - g.ly) / 2;
+            for (int y = y0; y < y0 + g.ly; ++y)
+                for (int x = x0; x < x0 + g.lx; ++x) lab[(size_t)y * nx + x] = LBM_BODY;
+            break;
+        }
+        case LBM_GEOM_MASK:
+            if (!g.mask) return set_error(LBM_EINVAL, "LBM_GEOM_MASK needs a mask");
+            for (size_t k = 0; k < lab.size(); ++k) {
+                if (g.mask[k] > LBM_WALL) return set_error(LBM_EINVAL, "mask label %d at %zu", g.mask[k], k);
+                lab[k] = g.mask[k];
+            }
+            break;
+        default:
+            return set_error(LBM_EINVAL, "unknown geometry kind %d", g.kind);
+    }
+    return LBM_OK;
+}
+
+static int gcd_int(int a, int b) {
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// For every fluid node, the links whose pull source, or a lattice node strictly between source and
+// node, is solid; the first solid node met walking back from the node decides body or wall.
+void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t>& lab, std::vector<uint8_t>& cls,
+                 std::vector<uint64_t>& body, std::vector<uint64_t>& wall, size_t& n_fluid, size_t& n_boundary) {
+    const size_t N = (size_t)nx * ny;
+    cls.assign(N, NODE_BULK);
+    body.assign(N, 0);
+    wall.assign(N, 0);
+    // solid within R (periodic) of each node: separable dilation
+    std::vector<uint8_t> rownear(N, 0), near(N, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            uint8_t v = 0;
+            for (int d = -H.R; d <= H.R && !v; ++d) v = lab[(size_t)y * nx + ((x + d) % nx + nx) % nx] != 0;
+            rownear[(size_t)y * nx + x] = v;
+        }
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            uint8_t v = 0;
+            for (int d = -H.R; d <= H.R && !v; ++d) v = rownear[(size_t)(((y + d) % ny + ny) % ny) * nx + x];
+            near[(size_t)y * nx + x] = v;
+        }
+    n_fluid = n_boundary = 0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t node = (size_t)y * nx + x;
+            if (lab[node]) { cls[node] = NODE_SOLID; continue; }
+            ++n_fluid;
+            if (!near[node]) continue;
+            uint64_t b = 0, w = 0;
+            for (int i = 1; i < H.Q; ++i) {
+                const int cx = H.c[i][0], cy = H.c[i][1];
+                const int g = gcd_int(std::abs(cx), std::abs(cy));
+                for (int k = 1; k <= g; ++k) {
+                    const int sx = ((x - k * cx / g) % nx + nx) % nx;
+                    const int sy = ((y - k * cy / g) % ny + ny) % ny;
+                    const uint8_t l = lab[(size_t)sy * nx + sx];
+                    if (l) {
+                        (l == LBM_BODY ? b : w) |= 1ull << i;
+                        break;
+                    }
+                }
+            }
+            body[node] = b;
+            wall[node] = w;
+            if (b | w) {
+                cls[node] = NODE_BOUNDARY;
+                ++n_boundary;
+            }
+        }
+}
+
+// Geometry-only part of the momentum exchange (the rest populations w_i rho0 bounced on body
+// links): -sum over body links of c_i 2 w_i rho0.
+void constant_force(const HostLattice& H, const std::vector<uint64_t>& body, double rho0, double& fx, double& fy) {
+    fx = fy = 0.0;
+    for (size_t node = 0; node < body.size(); ++node) {
+        const uint64_t b = body[node];
+        if (!b) continue;
+        for (int i = 1; i < H.Q; ++i)
+            if ((b >> i) & 1ull) {
+                fx -= H.c[i][0] * 2.0 * H.w[i] * rho0;
+                fy -= H.c[i][1] * 2.0 * H.w[i] * rho0;
+            }
+    }
+}
+
+void tile_slots(int nx, int ny, int bx, int by, const std::vector<uint64_t>& body, std::vector<int>& slot, int& ntx,
+                int& ntiles, int& nslots) {
+    ntx = (nx + bx - 1) / bx;
+    const int nty = (ny + by - 1) / by;
+    ntiles = ntx * nty;
+    slot.assign(ntiles, -1);
+    nslots = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        const int tx = t % ntx, ty = t / ntx;
+        bool any = false;
+        for (int y = ty * by; y < std::min(ny, (ty + 1) * by) && !any; ++y)
+            for (int x = tx * bx; x < std::min(nx, (tx + 1) * bx) && !any; ++x) any = body[(size_t)y * nx + x] != 0;
+        if (any) slot[t] = nslots++;
+    }
+}
+
+double drive_value(int drive, double u0, double omega, long n) {
+    const double t = (double)n + 0.5;
+    return drive == LBM_DRIVE_WALL ? u0 * std::sin(omega * t) : u0 * omega * std::cos(omega * t);
+}
+
+// ---------------------------------------------------------------------------------------------
+// fit (FP64 least squares on {sin, cos, 1})
+// ---------------------------------------------------------------------------------------------
+
+int fit_sincos(const double* fx, size_t stride, long n0, long n1, double omega, double coef[3]) {
+    double M[3][4] = {{0}};
+    for (long n = n0; n < n1; ++n) {
+        const double t = (double)n + 0.5;
+        const double b[3] = {std::sin(omega * t), std::cos(omega * t), 1.0};
+        const double y = fx[(size_t)n * stride];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) M[r][c] += b[r] * b[c];
+            M[r][3] += b[r] * y;
+        }
+    }
+    for (int c = 0; c < 3; ++c) {  // Gaussian elimination with partial pivoting
+        int p = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+        if (std::fabs(M[p][c]) < 1e-300) return set_error(LBM_ERANGE, "fit window too short");
+        if (p != c)
+            for (int k = 0; k < 4; ++k) std::swap(M[p][k], M[c][k]);
+        for (int r = 0; r < 3; ++r) {
+            if (r == c) continue;
+            const double f = M[r][c] / M[c][c];
+            for (int k = c; k < 4; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < 3; ++r) coef[r] = M[r][3] / M[r][r];
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+// ---------------------------------------------------------------------------------------------
+// the simulation object
+// ---------------------------------------------------------------------------------------------
+
+struct lbm_sim {
+    int device = 0;
+    int Q = 0, nx = 0, ny = 0, pitch = 0;
+    double tau = 0, omega = 0;
+    lbm_geometry geom{};
+    HostLattice lat{};
+    size_t esize = 0;
+    std::vector<uint8_t> labels;
+    std::vector<uint64_t> body_bits;
+    size_t n_fluid = 0, n_boundary = 0;
+    double fconst[2] = {0, 0};
+    // device memory
+    void* buf[2] = {nullptr, nullptr};
+    uint8_t* d_cls = nullptr;
+    ulonglong2* d_links = nullptr;
+    int* d_tile_slot = nullptr;
+    double2* d_partials = nullptr;
+    unsigned int* d_ticket = nullptr;
+    long long* d_step = nullptr;
+    int* d_err = nullptr;
+    double* d_drive = nullptr;
+    double2* d_history = nullptr;
+    size_t cap = 0;
+    size_t device_bytes = 0;
+    size_t h2d_bytes = 0, d2h_bytes = 0;  // host<->device traffic over the simulation's life
+    // state
+    long steps_done = 0;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int bx = 32, by = 4, ntx = 0, ntiles = 0, nslots = 0;
+    StepLaunchFn launch = nullptr;
+    InstDev dev{};
+};
+
+namespace {
+
+#define CUDA_TRY(expr)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            return set_error(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                             #expr, cudaGetErrorString(e_));                                     \
+        }                                                                                        \
+    } while (0)
+
+template <class T>
+int dev_alloc(lbm_sim* s, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    CUDA_TRY(cudaMalloc((void**)p, count * sizeof(T)));
+    s->device_bytes += count * sizeof(T);
+    return LBM_OK;
+}
+
+void free_sim(lbm_sim* s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaFree(s->buf[0]);
+    cudaFree(s->buf[1]);
+    cudaFree(s->d_cls);
+    cudaFree(s->d_links);
+    cudaFree(s->d_tile_slot);
+    cudaFree(s->d_partials);
+    cudaFree(s->d_ticket);
+    cudaFree(s->d_step);
+    cudaFree(s->d_err);
+    cudaFree(s->d_drive);
+    cudaFree(s->d_history);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+// (Re)build the per-tile force slots for the current tile shape.
+int setup_tiles(lbm_sim* s) {
+    std::vector<int> slot;
+    tile_slots(s->nx, s->ny, s->bx, s->by, s->body_bits, slot, s->ntx, s->ntiles, s->nslots);
+    cudaFree(s->d_tile_slot);
+    cudaFree(s->d_partials);
+    s->d_tile_slot = nullptr;
+    s->d_partials = nullptr;
+    int rc = dev_alloc(s, &s->d_tile_slot, slot.size());
+    if (rc) return rc;
+    rc = dev_alloc(s, &s->d_partials, (size_t)std::max(1, s->nslots));
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpy(s->d_tile_slot, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice));
+    s->h2d_bytes += slot.size() * sizeof(int);
+    CUDA_TRY(cudaMemset(s->d_partials, 0, (size_t)std::max(1, s->nslots) * sizeof(double2)));
+    s->dev.tile_slot = s->d_tile_slot;
+    s->dev.partials = s->d_partials;
+    s->dev.ntx = s->ntx;
+    s->dev.ntiles = s->ntiles;
+    s->dev.nslots = s->nslots;
+    return LBM_OK;
+}
+
+// Make room for the drive table and force history of `need` steps.
+int ensure_capacity(lbm_sim* s, size_t need) {
+    if (need <= s->cap) return LBM_OK;
+    size_t cap = std::max<size_t>(std::max<size_t>(need, 2 * s->cap), 1024);
+    double* drive = nullptr;
+    double2* hist = nullptr;
+    CUDA_TRY(cudaMalloc((void**)&drive, cap * sizeof(double)));
+    if (cudaMalloc((void**)&hist, cap * sizeof(double2)) != cudaSuccess) {
+        cudaFree(drive);
+        return set_error(LBM_ENOMEM, "force history of %zu steps", cap);
+    }
+    std::vector<double> table(cap);
+    for (size_t n = 0; n < cap; ++n) table[n] = drive_value(s->geom.drive, s->geom.u0, s->omega, (long)n);
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    CUDA_TRY(cudaMemcpy(drive, table.data(), cap * sizeof(double), cudaMemcpyHostToDevice));
+    s->h2d_bytes += cap * sizeof(double);
+    CUDA_TRY(cudaMemset(hist, 0, cap * sizeof(double2)));
+    if (s->d_history && s->steps_done > 0)
+        CUDA_TRY(cudaMemcpy(hist, s->d_history, (size_t)s->steps_done * sizeof(double2), cudaMemcpyDeviceToDevice));
+    cudaFree(s->d_drive);
+    cudaFree(s->d_history);
+    s->device_bytes += (cap - s->cap) * (sizeof(double) + sizeof(double2));
+    s->d_drive = drive;
+    s->d_history = hist;
+    s->cap = cap;
+    s->dev.drive = drive;
+    s->dev.history = hist;
+    return LBM_OK;
+}
+
+int check_sim(lbm_sim* s) {
+    if (!s) return set_error(LBM_EINVAL, "null simulation");
+    CUDA_TRY(cudaSetDevice(s->device));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return last_error(); }
+
+int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta) {
+    HostLattice H;
+    if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "unknown lattice %d", lattice);
+    for (int i = 0; i < H.Q; ++i) {
+        if (c_xy) { c_xy[2 * i] = H.c[i][0]; c_xy[2 * i + 1] = H.c[i][1]; }
+        if (w) w[i] = H.w[i];
+    }
+    if (theta) *theta = H.theta;
+    return H.Q;
+}
+
+int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, int p_min, double* tau,
+                              double* omega, int* period) {
+    HostLattice H;
+    if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "unknown lattice %d", lattice);
+    if (!(tau_omega > 0.0) || !(delta_min > 0.0) || p_min < 1)
+        return set_error(LBM_EINVAL, "need tau_omega > 0, delta_min > 0, p_min >= 1");
+    const double pi = 3.14159265358979323846;
+    const double need = std::ceil(2.0 * pi * delta_min / std::sqrt(2.0 * H.theta * tau_omega));
+    if (!(need < 2e9)) return set_error(LBM_EINVAL, "tau_omega %g needs too many steps per period", tau_omega);
+    const int P = std::max(p_min, (int)need);
+    const double om = 2.0 * pi / P;
+    if (tau) *tau = 0.5 + tau_omega / om;
+    if (omega) *omega = om;
+    if (period) *period = P;
+    return LBM_OK;
+}
+
+int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_geometry* geom, lbm_sim** out) {
+    clear_error();
+    if (!out) return set_error(LBM_EINVAL, "null output handle");
+    *out = nullptr;
+    if (!geom) return set_error(LBM_EINVAL, "null geometry");
+    HostLattice H;
+    if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "lattice must be LBM_D2Q9 or LBM_D2Q37");
+    if (nx < 2 * H.R + 1 || ny < 2 * H.R + 1)
+        return set_error(LBM_EINVAL, "grid %dx%d below %d nodes per side", nx, ny, 2 * H.R + 1);
+    if ((long long)nx * ny > (1ll << 31) / 2) return set_error(LBM_EINVAL, "grid %dx%d too large", nx, ny);
+    if (!(tau > 0.5) || !std::isfinite(tau)) return set_error(LBM_EINVAL, "tau must be > 1/2 (got %g)", tau);
+    if (!(omega > 0.0) || !std::isfinite(omega)) return set_error(LBM_EINVAL, "omega must be > 0 (got %g)", omega);
+    lbm_geometry g = *geom;
+    if (g.rho0 == 0.0) g.rho0 = 1.0;
+    if (!(g.rho0 > 0.0)) return set_error(LBM_EINVAL, "rho0 must be > 0");
+    if (!(g.u0 >= 0.0) || !(g.u0 < omega))
+        return set_error(LBM_EINVAL, "need 0 <= u0 < omega (displacement below one node), got u0=%g omega=%g", g.u0,
+                         omega);
+    if (g.drive != LBM_DRIVE_WALL && g.drive != LBM_DRIVE_BODYFORCE) return set_error(LBM_EINVAL, "bad drive");
+    if (g.eq_order != 2 && g.eq_order != 4) return set_error(LBM_EINVAL, "eq_order must be 2 or 4");
+    if (lattice == LBM_D2Q9 && g.eq_order != 2) return set_error(LBM_EINVAL, "D2Q9 supports eq_order 2 only");
+    if (g.collision != LBM_COLL_BGK && g.collision != LBM_COLL_REGULARIZED)
+        return set_error(LBM_EINVAL, "bad collision");
+    const size_t es = storage_size(g.storage);
+    if (!es) return set_error(LBM_EINVAL, "bad storage type %d", g.storage);
+    if (es == 2 && !(g.u0 > 0.0))
+        return set_error(LBM_EINVAL, "16-bit storage is scaled by u0 and needs u0 > 0");
+    StepLaunchFn fn = find_step_launcher(lattice, g.storage, g.collision);
+    if (!fn) return set_error(LBM_EINVAL, "no kernel for this lattice/storage/collision");
+
+    lbm_sim* s = new (std::nothrow) lbm_sim();
+    if (!s) return set_error(LBM_ENOMEM, "host allocation");
+    s->Q = lattice;
+    s->nx = nx;
+    s->ny = ny;
+    s->tau = tau;
+    s->omega = omega;
+    s->lat = H;
+    s->esize = es;
+    s->launch = fn;
+    int rc = cudaGetDevice(&s->device) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    if (rc) { delete s; return set_error(rc, "no CUDA device"); }
+    rc = build_labels(lattice, nx, ny, g, s->labels);
+    if (rc) { delete s; return rc; }
+    g.mask = nullptr;
+    s->geom = g;
+    std::vector<uint8_t> cls;
+    std::vector<uint64_t> wall;
+    build_links(H, nx, ny, s->labels, cls, s->body_bits, wall, s->n_fluid, s->n_boundary);
+    constant_force(H, s->body_bits, g.rho0, s->fconst[0], s->fconst[1]);
+
+    const int align = (int)(128 / es);
+    s->pitch = (nx + align - 1) / align * align;
+    const size_t plane = (size_t)ny * s->pitch;
+
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return set_error(LBM_ECUDA, "stream creation failed");
+    }
+    s->own_stream = true;
+
+#define TRY_OR_FREE(x)          \
+    do {                        \
+        int r_ = (x);           \
+        if (r_) {               \
+            free_sim(s);        \
+            return r_;          \
+        }                       \
+    } while (0)
+
+    for (int b = 0; b < 2; ++b) {
+        TRY_OR_FREE(dev_alloc(s, (char**)&s->buf[b], plane * H.Q * es));
+        if (cudaMemset(s->buf[b], 0, plane * H.Q * es) != cudaSuccess) {
+            free_sim(s);
+            return set_error(LBM_ECUDA, "memset");
+        }
+    }
+    // node classes and link masks in the padded layout
+    std::vector<uint8_t> cls_p(plane, NODE_SOLID);
+    std::vector<ulonglong2> links_p(plane, make_ulonglong2(0, 0));
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t k = (size_t)y * nx + x, kp = (size_t)y * s->pitch + x;
+            cls_p[kp] = cls[k];
+            links_p[kp] = make_ulonglong2(s->body_bits[k], wall[k]);
+        }
+    TRY_OR_FREE(dev_alloc(s, &s->d_cls, plane));
+    TRY_OR_FREE(dev_alloc(s, &s->d_links, plane));
+    TRY_OR_FREE(dev_alloc(s, &s->d_ticket, 1));
+    TRY_OR_FREE(dev_alloc(s, &s->d_step, 1));
+    TRY_OR_FREE(dev_alloc(s, &s->d_err, 1));
+    if (cudaMemcpy(s->d_cls, cls_p.data(), plane, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->d_links, links_p.data(), plane * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s->d_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(s->d_step, 0, sizeof(long long)) != cudaSuccess ||
+        cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
+        free_sim(s);
+        return set_error(LBM_ECUDA, "upload of geometry failed");
+    }
+    s->h2d_bytes += plane * (1 + sizeof(ulonglong2));
+
+    InstDev& d = s->dev;
+    d.cls = s->d_cls;
+    d.links = s->d_links;
+    d.ticket = s->d_ticket;
+    d.step = s->d_step;
+    d.err = s->d_err;
+    d.fconst = make_double2(s->fconst[0], s->fconst[1]);
+    d.plane = (long long)plane;
+    d.nx = nx;
+    d.ny = ny;
+    d.pitch = s->pitch;
+    d.eq_order = g.eq_order;
+    d.moving = g.drive == LBM_DRIVE_WALL;
+    d.body_force = g.drive == LBM_DRIVE_BODYFORCE;
+    d.rho0 = g.rho0;
+    d.s = es == 2 ? g.u0 : 1.0;
+    d.inv_s = 1.0 / d.s;
+    d.omega_c = 1.0 / tau;
+    d.reg_a = (1.0 - 1.0 / tau) / (2.0 * H.theta * H.theta);
+    d.src_k = (1.0 - 0.5 / tau) / H.theta;
+    d.mw_k = 2.0 * g.rho0 / (H.theta * d.s);
+    TRY_OR_FREE(setup_tiles(s));
+    TRY_OR_FREE(ensure_capacity(s, 1024));
+    *out = s;
+    return LBM_OK;
+}
+
+int lbm_set_tile(lbm_sim* s, int block_x, int block_y) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (block_x < 32 || block_x % 32 || block_y < 1 || block_x * block_y > 512)
+        return set_error(LBM_EINVAL, "tile %dx%d: need block_x a multiple of 32 and block_x*block_y <= 512", block_x,
+                         block_y);
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->bx = block_x;
+    s->by = block_y;
+    return setup_tiles(s);
+}
+
+int lbm_step(lbm_sim* s, long n) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (n < 0) return set_error(LBM_EINVAL, "negative step count");
+    if (n == 0) return LBM_OK;
+    rc = ensure_capacity(s, (size_t)(s->steps_done + n));
+    if (rc) return rc;
+    const dim3 block(s->bx, s->by);
+    for (long k = 0; k < n; ++k) {
+        s->dev.src = s->buf[s->cur];
+        s->dev.dst = s->buf[s->cur ^ 1];
+        const cudaError_t e = s->launch(s->dev, block, s->stream);
+        if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
+        s->cur ^= 1;
+        ++s->steps_done;
+    }
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_sim* s) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 1) return set_error(LBM_ENONFINITE, "force became non-finite: the run diverged");
+    return LBM_OK;
+}
+
+int lbm_force_history(lbm_sim* s, double* out_xy, size_t cap_steps, size_t* n_steps) {
+    int rc = lbm_synchronize(s);
+    if (rc && rc != LBM_ENONFINITE) return rc;
+    if (n_steps) *n_steps = (size_t)s->steps_done;
+    const size_t n = std::min(cap_steps, (size_t)s->steps_done);
+    if (n && !out_xy) return set_error(LBM_EINVAL, "null output buffer");
+    if (n) CUDA_TRY(cudaMemcpy(out_xy, s->d_history, n * sizeof(double2), cudaMemcpyDeviceToHost));
+    s->d2h_bytes += n * sizeof(double2);
+    return rc;
+}
+
+int lbm_fit(lbm_sim* s, double skip_periods, double* f_in, double* f_q, double* f_0) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    const double pi = 3.14159265358979323846;
+    const double period = 2.0 * pi / s->omega;
+    if (!(skip_periods >= 0.0)) return set_error(LBM_EINVAL, "skip_periods must be >= 0");
+    const long n0 = (long)std::ceil(skip_periods * period);
+    if ((double)(s->steps_done - n0) < period) return set_error(LBM_ERANGE, "less than one period after the skip");
+    std::vector<double> h(2 * (size_t)s->steps_done);
+    size_t n = 0;
+    rc = lbm_force_history(s, h.data(), (size_t)s->steps_done, &n);
+    if (rc) return rc;
+    double coef[3];
+    rc = fit_sincos(h.data(), 2, n0, s->steps_done, s->omega, coef);
+    if (rc) return rc;
+    const double sgn = s->geom.drive == LBM_DRIVE_WALL ? 1.0 : -1.0;
+    if (f_in) *f_in = sgn * coef[0];
+    if (f_q) *f_q = sgn * coef[1];
+    if (f_0) *f_0 = coef[2];
+    return LBM_OK;
+}
+
+int lbm_gamma_bar(lbm_sim* s, double f_in, double perimeter, double* gamma_bar) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!gamma_bar || !(perimeter > 0.0) || !(s->geom.u0 > 0.0))
+        return set_error(LBM_EINVAL, "need an output, perimeter > 0 and u0 > 0");
+    *gamma_bar = -f_in / (s->geom.u0 * s->geom.rho0 * std::sqrt(s->lat.theta / 2.0) * perimeter);
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_sim* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    free_sim(s);
+}
+
+int lbm_set_stream(lbm_sim* s, void* stream) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    s->stream = (cudaStream_t)stream;
+    s->own_stream = false;
+    return LBM_OK;
+}
+
+static double to_double(const void* base, int storage, size_t k) {
+    switch (storage) {
+        case ST_F64: return static_cast<const double*>(base)[k];
+        case ST_F32: return static_cast<const float*>(base)[k];
+        case ST_BF16: return (double)__bfloat162float(static_cast<const __nv_bfloat16*>(base)[k]);
+        default: return (double)__half2float(static_cast<const __half*>(base)[k]);
+    }
+}
+
+static void from_double(void* base, int storage, size_t k, double v) {
+    switch (storage) {
+        case ST_F64: static_cast<double*>(base)[k] = v; break;
+        case ST_F32: static_cast<float*>(base)[k] = (float)v; break;
+        case ST_BF16: static_cast<__nv_bfloat16*>(base)[k] = __double2bfloat16(v); break;
+        default: static_cast<__half*>(base)[k] = __double2half(v); break;
+    }
+}
+
+int lbm_get_state(lbm_sim* s, double* out, size_t count) {
+    int rc = lbm_synchronize(s);
+    if (rc && rc != LBM_ENONFINITE) return rc;
+    const size_t N = (size_t)s->nx * s->ny, plane = (size_t)s->ny * s->pitch;
+    if (!out || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
+    std::vector<unsigned char> host(plane * s->Q * s->esize);
+    CUDA_TRY(cudaMemcpy(host.data(), s->buf[s->cur], host.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < s->Q; ++i) {
+        const double scale = s->lat.w[i] * s->dev.s;
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x)
+                out[(size_t)i * N + (size_t)y * s->nx + x] =
+                    scale * to_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x);
+    }
+    return rc;
+}
+
+int lbm_set_state(lbm_sim* s, const double* g, size_t count) {
+    int rc = lbm_synchronize(s);
+    if (rc) return rc;
+    const size_t N = (size_t)s->nx * s->ny, plane = (size_t)s->ny * s->pitch;
+    if (!g || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
+    std::vector<unsigned char> host(plane * s->Q * s->esize, 0);
+    for (int i = 0; i < s->Q; ++i) {
+        const double inv = 1.0 / (s->lat.w[i] * s->dev.s);
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                const size_t k = (size_t)y * s->nx + x;
+                const double v = s->labels[k] ? 0.0 : g[(size_t)i * N + k] * inv;
+                from_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x, v);
+            }
+    }
+    CUDA_TRY(cudaMemcpy(s->buf[s->cur], host.data(), host.size(), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+int lbm_get_labels(lbm_sim* s, unsigned char* out, size_t count) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!out || count != s->labels.size()) return set_error(LBM_ERANGE, "need %zu labels", s->labels.size());
+    std::memcpy(out, s->labels.data(), count);
+    return LBM_OK;
+}
+
+int lbm_info(lbm_sim* s, lbm_info_t* o) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (!o) return set_error(LBM_EINVAL, "null output");
+    o->lattice = s->Q;
+    o->nx = s->nx;
+    o->ny = s->ny;
+    o->pitch = s->pitch;
+    o->storage = s->geom.storage;
+    o->collision = s->geom.collision;
+    o->eq_order = s->geom.eq_order;
+    o->drive = s->geom.drive;
+    o->tau = s->tau;
+    o->omega = s->omega;
+    o->u0 = s->geom.u0;
+    o->rho0 = s->geom.rho0;
+    o->theta = s->lat.theta;
+    o->steps_done = s->steps_done;
+    o->n_fluid = s->n_fluid;
+    o->n_boundary = s->n_boundary;
+    o->bytes_per_step = 2 * (size_t)s->Q * s->esize * s->n_fluid;
+    o->device_bytes = s->device_bytes;
+    o->block_x = s->bx;
+    o->block_y = s->by;
+    o->h2d_bytes = s->h2d_bytes;
+    o->d2h_bytes = s->d2h_bytes;
+    return LBM_OK;
+}
+
+}  // extern "C"

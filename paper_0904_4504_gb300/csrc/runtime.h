@@ -1,0 +1,35 @@
+// runtime.h -- host-side helpers shared by the C-ABI translation units (not part of the ABI).
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "lbm.h"
+
+namespace lbm {
+
+struct HostLattice {
+    int Q = 0, R = 0;
+    double theta = 0;
+    int c[37][2] = {};
+    double w[37] = {};
+    int opp[37] = {};
+};
+
+bool host_lattice(int Q, HostLattice& H);
+size_t storage_size(int storage);
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+const char* last_error();
+int build_labels(int Q, int nx, int ny, const lbm_geometry& g, std::vector<uint8_t>& lab);
+void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t>& lab, std::vector<uint8_t>& cls,
+                 std::vector<uint64_t>& body, std::vector<uint64_t>& wall, size_t& n_fluid, size_t& n_boundary);
+void constant_force(const HostLattice& H, const std::vector<uint64_t>& body, double rho0, double& fx, double& fy);
+void tile_slots(int nx, int ny, int bx, int by, const std::vector<uint64_t>& body, std::vector<int>& slot, int& ntx,
+                int& ntiles, int& nslots);
+double drive_value(int drive, double u0, double omega, long n);
+int fit_sincos(const double* fx, size_t stride, long n0, long n1, double omega, double coef[3]);
+
+}  // namespace lbm

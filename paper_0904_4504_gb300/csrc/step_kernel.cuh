@@ -1,0 +1,345 @@
+// step_kernel.cuh -- the fused LBGK time step on sm_103a.
+//
+// One launch performs, for every fluid node of one or more lattices (Sec. 5 of the paper, in its
+// order): advection by pull (Eq. 17) with bounce-back on blocked links (Eq. 12), the moments
+// (Eq. 16), the Hermite equilibrium (Eq. 15 or its 4th-order continuation), the regularized
+// collision (Eqs. 18-19) or the plain BGK step (Eq. 14), an optional body force, and the store.
+// The momentum given to the body by bounce-back is reduced in FP64 (warp shuffles, then a fixed
+// slot per tile); the last tile of an instance to finish sums the slots in a fixed order, appends
+// (Fx, Fy) to the force history and advances the instance's step counter.  No block ever waits
+// for another.
+//
+// Storage.  Populations are kept as scaled deviations from the rest state,
+//     h_i = (f_i - w_i rho0) / (w_i s),
+// structure-of-arrays [Q][ny][pitch].  s = 1 for FP64/FP32 storage and s = u0 (the drive
+// amplitude) for BF16/FP16, so that every direction is O(1) and far from the 16-bit subnormal
+// range.  The weights cancel out of the equilibrium and collision in these units.  Arithmetic is
+// FP64 for FP64 storage and FP32 otherwise; the wall force is always accumulated in FP64.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_F16 = 3 };
+enum Collision { COLL_BGK = 0, COLL_REG = 1 };
+
+// Node classes of the `cls` array.
+enum NodeClass : uint8_t { NODE_BULK = 0, NODE_SOLID = 1, NODE_BOUNDARY = 2 };
+
+// Everything one launch needs to know about one lattice instance.
+struct InstDev {
+    const void* src;             // h at step n, [Q][ny][pitch]
+    void* dst;                   // h at step n+1
+    const uint8_t* cls;          // [ny][pitch] NodeClass
+    const ulonglong2* links;     // [ny][pitch]: .x bit i = link i blocked by the body (label 1),
+                                 //              .y bit i = blocked by a static wall (label 2)
+    const int* tile_slot;        // [ntiles] force-partial slot of a tile, -1 if it has no body link
+    double2* partials;           // [nslots] per-tile FP64 force partials
+    unsigned int* ticket;        // tiles of the current step that have finished
+    long long* step;             // device step counter n
+    const double* drive;         // [capacity] U_w(n + 1/2) (wall drive) or g(n + 1/2) (body force)
+    double2* history;            // [capacity] force on the body during step n
+    int* err;                    // bit 0: non-finite force seen
+    double2 fconst;              // geometry-only part of the force, -sum c_i 2 w_i rho0
+    long long plane;             // ny * pitch
+    int nx, ny, pitch;
+    int ntx;                     // tiles along x
+    int ntiles, nslots;
+    int eq_order;                // 2 or 4
+    int moving;                  // 1: body links carry the moving-wall term (wall drive)
+    int body_force;              // 1: fluid gets rho * g (body-frame drive)
+    double rho0;
+    double s, inv_s;             // storage scale
+    double omega_c;              // 1/tau
+    double reg_a;                // (1 - 1/tau) / (2 theta^2)
+    double src_k;                // (1 - 1/(2 tau)) / theta
+    double mw_k;                 // 2 rho0 / (theta s): moving-wall term per unit c_i.U_w
+};
+
+template <class ST> struct StoreT;
+template <> struct StoreT<double> {
+    using CT = double;
+    static __device__ __forceinline__ double ld(const double* p) { return *p; }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct StoreT<float> {
+    using CT = float;
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <> struct StoreT<__nv_bfloat16> {
+    using CT = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct StoreT<__half> {
+    using CT = float;
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// Advection + bounce-back + collision of the fluid node (x, y).  Adds the momentum the node's
+// blocked body links hand to the body to (Fx, Fy).
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void node_update(const InstDev& P, int x, int y, int cls, double dv, double& Fx,
+                                            double& Fy) {
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    constexpr int Q = L::Q, R = L::R, NP = L::NP;
+    constexpr bool SCALED = sizeof(ST) == 2;
+    const ST* __restrict__ src = static_cast<const ST*>(P.src);
+    ST* __restrict__ dst = static_cast<ST*>(P.dst);
+    const long long plane = P.plane;
+    const int idx = y * P.pitch + x;
+
+    // periodic wrap of the pull sources
+    int roff[2 * R + 1], col[2 * R + 1];
+#pragma unroll
+    for (int d = -R; d <= R; ++d) {
+        int ys = y - d;
+        ys += ys < 0 ? P.ny : 0;
+        ys -= ys >= P.ny ? P.ny : 0;
+        int xs = x - d;
+        xs += xs < 0 ? P.nx : 0;
+        xs -= xs >= P.nx ? P.nx : 0;
+        roff[d + R] = ys * P.pitch;
+        col[d + R] = xs;
+    }
+
+    // Eq. 17: h_i^adv(x) = h_i(x - c_i)
+    T h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of<L>(i), cy = cy_of<L>(i);
+        h[i] = S::ld(src + i * plane + roff[cy + R] + col[cx + R]);
+    }
+
+    // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
+    // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
+    if (cls == NODE_BOUNDARY) {
+        const ulonglong2 lk = P.links[idx];
+        const unsigned long long blk = lk.x | lk.y;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if ((blk >> i) & 1ull) {
+                const int cx = cx_of<L>(i), cy = cy_of<L>(i);
+                const T own = S::ld(src + opp_of<L>(i) * plane + idx);
+                double mw = 0.0;
+                if ((lk.x >> i) & 1ull) {
+                    if (P.moving) mw = P.mw_k * cx * dv;
+                    // momentum c_opp h_opp in, c_i h_i^adv out: -c_i w_i s (h_opp + h_i^adv)
+                    const double hs = 2.0 * (double)own + mw;
+                    const double ws = w_of<L>(i) * P.s;
+                    Fx -= cx * ws * hs;
+                    Fy -= cy * ws * hs;
+                }
+                h[i] = own + (T)mw;
+            }
+        }
+    }
+
+    // Eq. 16 on deviations: drho = sum g_i, j = sum g_i c_i, Pi' = sum g_i c_i c_i
+    T m0 = (T)L::w0() * h[0], jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int px = L::px(k), py = L::py(k);
+        const double w = L::wp(k);
+        const T sp = h[1 + 2 * k] + h[2 + 2 * k];
+        const T dm = h[1 + 2 * k] - h[2 + 2 * k];
+        m0 += (T)w * sp;
+        if (px) jx += (T)(w * px) * dm;
+        if (py) jy += (T)(w * py) * dm;
+        if (px) pxx += (T)(w * px * px) * sp;
+        if (px && py) pxy += (T)(w * px * py) * sp;
+        if (py) pyy += (T)(w * py * py) * sp;
+    }
+    if (SCALED) {
+        const T s = (T)P.s;
+        m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
+    }
+    constexpr double TH = L::theta();
+    const T th = (T)TH, ith = (T)(1.0 / TH);
+    const T drho = m0;
+    const T rho = (T)P.rho0 + drho;
+    const T irho = (T)1 / rho;
+    const T Fbx = P.body_force ? rho * (T)dv : (T)0;
+    const T ux = (jx + (T)0.5 * Fbx) * irho;
+    const T uy = jy * irho;
+    const T ax = ux * ith, ay = uy * ith;
+    const T b = (ux * ux + uy * uy) * ith;
+
+    // Eq. 15 (+ 4th order): g_i^eq / w_i = E(a^2) + O(a), a = c_i.u/theta
+    T e0 = drho - (T)0.5 * rho * b, e1 = (T)0.5 * rho, e2 = 0, o0 = rho, o1 = 0;
+    if (P.eq_order >= 4) {
+        e0 += (T)0.125 * rho * b * b;
+        e1 -= (T)0.25 * rho * b;
+        e2 = rho * (T)(1.0 / 24.0);
+        o0 -= (T)0.5 * rho * b;
+        o1 = rho * (T)(1.0 / 6.0);
+    }
+    // Guo-type source, even part kf (a c_x - u_x) and odd part c_x * (kf or F/(2 theta))
+    const T kf = (T)P.src_k * Fbx;
+    const T kfu = -kf * ux;
+    const T inv_s = SCALED ? (T)P.inv_s : (T)1;
+
+    if (COLL == COLL_REG) {
+        // Eq. 19: Pi^ne = Pi - Pi^eq with Pi^eq = rho theta I + rho u u (exact on these lattices)
+        const T Pxx = pxx - drho * th - rho * ux * ux;
+        const T Pxy = pxy - rho * ux * uy;
+        const T Pyy = pyy - drho * th - rho * uy * uy;
+        const T A = (T)P.reg_a;
+        const T rxx = A * Pxx, rxy = (T)2 * A * Pxy, ryy = A * Pyy;
+        const T c0 = e0 - A * th * (Pxx + Pyy) + kfu;
+        const T hf = (T)0.5 * Fbx * ith;   // first-order part: kept J^ne = -F/2 plus the source
+        S::st(dst + idx, c0 * inv_s);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int px = L::px(k), py = L::py(k);
+            T a = 0;
+            if (px) a += (T)px * ax;
+            if (py) a += (T)py * ay;
+            const T a2 = a * a;
+            T E = c0 + a2 * (e1 + a2 * e2);
+            if (px) E += (T)(px * px) * rxx;
+            if (px && py) E += (T)(px * py) * rxy;
+            if (py) E += (T)(py * py) * ryy;
+            if (px) E += a * ((T)px * kf);
+            T O = a * (o0 + o1 * a2);
+            if (px) O += (T)px * hf;
+            // Eq. 18: f = f^eq + (1 - 1/tau) f^ne (+ source)
+            S::st(dst + (1 + 2 * k) * plane + idx, (E + O) * inv_s);
+            S::st(dst + (2 + 2 * k) * plane + idx, (E - O) * inv_s);
+        }
+    } else {
+        const T om = (T)P.omega_c;
+        S::st(dst + idx, h[0] + om * (e0 * inv_s - h[0]) + kfu * inv_s);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int px = L::px(k), py = L::py(k);
+            T a = 0;
+            if (px) a += (T)px * ax;
+            if (py) a += (T)py * ay;
+            const T a2 = a * a;
+            const T E = e0 + a2 * (e1 + a2 * e2);
+            const T O = a * (o0 + o1 * a2);
+            T Es = kfu, Os = 0;
+            if (px) { Es += a * ((T)px * kf); Os = (T)px * kf; }
+            const T hp = h[1 + 2 * k], hm = h[2 + 2 * k];
+            // Eq. 14 discretized: f - (f - f^eq)/tau + source
+            S::st(dst + (1 + 2 * k) * plane + idx, hp + om * ((E + O) * inv_s - hp) + (Es + Os) * inv_s);
+            S::st(dst + (2 + 2 * k) * plane + idx, hm + om * ((E - O) * inv_s - hm) + (Es - Os) * inv_s);
+        }
+    }
+}
+
+// Force partial of a tile (fixed-order reduction), then the last tile of the instance finishes
+// the step: history[n] = sum of slots (fixed order) + constant part, n <- n + 1.
+__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double Fx, double Fy) {
+    __shared__ double2 red[32];
+    __shared__ int last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+    const int slot = P.tile_slot[tile];
+    if (slot >= 0) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            Fx += __shfl_down_sync(0xffffffffu, Fx, o);
+            Fy += __shfl_down_sync(0xffffffffu, Fy, o);
+        }
+        if ((tid & 31) == 0) red[tid >> 5] = make_double2(Fx, Fy);
+        __syncthreads();
+        if (tid < 32) {
+            double2 v = tid < nwarps ? red[tid] : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+            }
+            if (tid == 0) P.partials[slot] = v;
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(P.ticket, 1u);
+        last = (t == (unsigned)(P.ntiles - 1));
+    }
+    __syncthreads();
+    if (last && tid < 32) {
+        __threadfence();
+        double sx = 0.0, sy = 0.0;
+        for (int k = tid; k < P.nslots; k += 32) {
+            const double2 v = __ldcg(P.partials + k);
+            sx += v.x;
+            sy += v.y;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+        }
+        if (tid == 0) {
+            const long long n = *P.step;
+            const double2 F = make_double2(sx + P.fconst.x, sy + P.fconst.y);
+            if (!isfinite(F.x) || !isfinite(F.y)) atomicOr(P.err, 1);
+            P.history[n] = F;
+            *P.ticket = 0u;
+            *P.step = n + 1;
+        }
+    }
+}
+
+// One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void process_tile(const InstDev& P, int tile) {
+    const int tx = tile % P.ntx, ty = tile / P.ntx;
+    const int x = tx * blockDim.x + threadIdx.x;
+    const int y = ty * blockDim.y + threadIdx.y;
+    const double dv = P.drive[*P.step];
+    double Fx = 0.0, Fy = 0.0;
+    const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, x, y, cls, dv, Fx, Fy);
+    tile_epilogue(P, tile, Fx, Fy);
+}
+
+// Single-instance step: one block per tile.
+template <class L, class ST, int COLL>
+__global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
+    process_tile<L, ST, COLL>(P, blockIdx.x);
+}
+
+// Batched step: block b works on tile tiles[b].y of instance tiles[b].x.
+template <class L, class ST, int COLL>
+__global__ void __launch_bounds__(512) step_kernel_batched(const InstDev* __restrict__ insts,
+                                                           const int2* __restrict__ tiles) {
+    const int2 t = tiles[blockIdx.x];
+    process_tile<L, ST, COLL>(insts[t.x], t.y);
+}
+
+using StepLaunchFn = cudaError_t (*)(const InstDev& P, dim3 block, cudaStream_t stream);
+using BatchLaunchFn = cudaError_t (*)(const InstDev* insts, const int2* tiles, int nblocks, dim3 block,
+                                      cudaStream_t stream);
+
+template <class L, class ST, int COLL>
+cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
+    step_kernel<L, ST, COLL><<<P.ntiles, block, 0, stream>>>(P);
+    return cudaGetLastError();
+}
+
+template <class L, class ST, int COLL>
+cudaError_t launch_step_batched(const InstDev* insts, const int2* tiles, int nblocks, dim3 block,
+                                cudaStream_t stream) {
+    step_kernel_batched<L, ST, COLL><<<nblocks, block, 0, stream>>>(insts, tiles);
+    return cudaGetLastError();
+}
+
+// Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.
+StepLaunchFn find_step_launcher(int Q, int storage, int coll);
+BatchLaunchFn find_batch_launcher(int Q, int storage, int coll);
+
+}  // namespace lbm

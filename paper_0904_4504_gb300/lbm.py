@@ -1,0 +1,269 @@
+"""Python binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every function keeps its C name and argument order; numpy arrays stand in for host pointers, and
+a torch stream (or its raw handle) for the cudaStream_t of lbm_set_stream.  All arithmetic of the
+time step runs in the CUDA library: if liblbm.so is missing this module raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+
+from .builder import LIB, INCLUDE
+
+LBM_OK = 0
+LBM_EINVAL = -1
+LBM_ENOMEM = -2
+LBM_ECUDA = -3
+LBM_ETIMEOUT = -4
+LBM_ENONFINITE = -5
+LBM_ERANGE = -6
+
+LBM_D2Q9, LBM_D2Q37 = 9, 37
+LBM_GEOM_PLATE, LBM_GEOM_BEAM, LBM_GEOM_MASK, LBM_GEOM_NONE = 0, 1, 2, 3
+LBM_DRIVE_WALL, LBM_DRIVE_BODYFORCE = 0, 1
+LBM_COLL_BGK, LBM_COLL_REGULARIZED = 0, 1
+LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = 0, 1, 2, 3
+LBM_FLUID, LBM_BODY, LBM_WALL = 0, 1, 2
+STORAGE_BYTES = {LBM_STORE_F64: 8, LBM_STORE_F32: 4, LBM_STORE_BF16: 2, LBM_STORE_F16: 2}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class lbm_geometry(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("lx", ctypes.c_int),
+        ("ly", ctypes.c_int),
+        ("drive", ctypes.c_int),
+        ("u0", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("mask", ctypes.POINTER(ctypes.c_ubyte)),
+        ("eq_order", ctypes.c_int),
+        ("collision", ctypes.c_int),
+        ("storage", ctypes.c_int),
+    ]
+
+
+class lbm_info_t(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int),
+        ("storage", ctypes.c_int), ("collision", ctypes.c_int), ("eq_order", ctypes.c_int), ("drive", ctypes.c_int),
+        ("tau", ctypes.c_double), ("omega", ctypes.c_double), ("u0", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("steps_done", ctypes.c_long),
+        ("n_fluid", ctypes.c_size_t), ("n_boundary", ctypes.c_size_t),
+        ("bytes_per_step", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
+        ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+        ("h2d_bytes", ctypes.c_size_t), ("d2h_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/*.h declares."""
+    names = []
+    for h in sorted(Path(INCLUDE).glob("*.h")):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*(lbm_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return names
+
+
+def lib():
+    """The loaded liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not Path(LIB).exists():
+            raise RuntimeError(f"{LIB} is missing: build it with paper_0904_4504_gb300.builder.build()")
+        L = ctypes.CDLL(str(LIB))
+        sig = {
+            "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(lbm_geometry), ctypes.POINTER(_P)]),
+            "lbm_step": (ctypes.c_int, [_P, ctypes.c_long]),
+            "lbm_synchronize": (ctypes.c_int, [_P]),
+            "lbm_force_history": (ctypes.c_int, [_P, _D, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+            "lbm_fit": (ctypes.c_int, [_P, ctypes.c_double, _D, _D, _D]),
+            "lbm_gamma_bar": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _D]),
+            "lbm_destroy": (None, [_P]),
+            "lbm_last_error": (ctypes.c_char_p, []),
+            "lbm_set_stream": (ctypes.c_int, [_P, _P]),
+            "lbm_get_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t]),
+            "lbm_set_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t]),
+            "lbm_get_labels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ubyte), ctypes.c_size_t]),
+            "lbm_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_info_t)]),
+            "lbm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+            "lbm_lattice_velocities": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D]),
+            "lbm_params_from_tau_omega": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                         _D, _D, ctypes.POINTER(ctypes.c_int)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise LbmError(rc, lib().lbm_last_error().decode())
+    return rc
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+# ------------------------------------------------------------------------------------------------
+# the C functions, same names
+# ------------------------------------------------------------------------------------------------
+
+def lbm_last_error() -> str:
+    return lib().lbm_last_error().decode()
+
+
+def lbm_lattice_velocities(lattice: int):
+    """(c (Q, 2) int, w (Q,), theta) in the library's direction order."""
+    Q = _check(lib().lbm_lattice_velocities(lattice, None, None, None))
+    c = (ctypes.c_int * (2 * Q))()
+    w = np.zeros(Q)
+    th = ctypes.c_double()
+    _check(lib().lbm_lattice_velocities(lattice, c, _dp(w), ctypes.byref(th)))
+    return np.array(c[:], dtype=np.int64).reshape(Q, 2), w, th.value
+
+
+def lbm_params_from_tau_omega(lattice: int, tau_omega: float, delta_min: float = 4.0, p_min: int = 128):
+    """(tau, omega, period) for a nondimensional frequency tau*omega."""
+    tau, om, P = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().lbm_params_from_tau_omega(lattice, tau_omega, delta_min, p_min, ctypes.byref(tau), ctypes.byref(om),
+                                           ctypes.byref(P)))
+    return tau.value, om.value, P.value
+
+
+def make_geometry(kind=LBM_GEOM_NONE, lx=0, ly=0, drive=LBM_DRIVE_WALL, u0=0.0, rho0=1.0, mask=None, eq_order=2,
+                  collision=LBM_COLL_REGULARIZED, storage=LBM_STORE_F32):
+    """An lbm_geometry; `mask` (ny x nx uint8) is kept alive on the returned object."""
+    g = lbm_geometry(kind, lx, ly, drive, u0, rho0, None, eq_order, collision, storage)
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        g._mask_ref = m
+        g.mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+    return g
+
+
+def lbm_create(lattice: int, nx: int, ny: int, tau: float, omega: float, geom: lbm_geometry) -> int:
+    h = _P()
+    _check(lib().lbm_create(lattice, nx, ny, tau, omega, ctypes.byref(geom), ctypes.byref(h)))
+    return h.value
+
+
+def lbm_step(sim: int, n: int) -> None:
+    _check(lib().lbm_step(sim, n))
+
+
+def lbm_synchronize(sim: int) -> None:
+    _check(lib().lbm_synchronize(sim))
+
+
+def lbm_force_history(sim: int, cap_steps: int | None = None) -> np.ndarray:
+    """(steps, 2) FP64 array of (Fx, Fy)."""
+    n = ctypes.c_size_t()
+    _check(lib().lbm_force_history(sim, None, 0, ctypes.byref(n)))
+    cap = n.value if cap_steps is None else min(cap_steps, n.value)
+    out = np.zeros((cap, 2))
+    _check(lib().lbm_force_history(sim, _dp(out), cap, ctypes.byref(n)))
+    return out
+
+
+def lbm_fit(sim: int, skip_periods: float):
+    """(f_in, f_q, f_0)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().lbm_fit(sim, skip_periods, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def lbm_gamma_bar(sim: int, f_in: float, perimeter: float) -> float:
+    g = ctypes.c_double()
+    _check(lib().lbm_gamma_bar(sim, f_in, perimeter, ctypes.byref(g)))
+    return g.value
+
+
+def lbm_destroy(sim: int) -> None:
+    if sim:
+        lib().lbm_destroy(sim)
+
+
+def lbm_set_stream(sim: int, stream=None) -> None:
+    """`stream`: a torch.cuda.Stream or a raw cudaStream_t handle (None or 0: the default stream)."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().lbm_set_stream(sim, handle or None))
+
+
+def lbm_info(sim: int) -> dict:
+    o = lbm_info_t()
+    _check(lib().lbm_info(sim, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def lbm_get_state(sim: int) -> np.ndarray:
+    """Deviations g = f - w rho0 as a (Q, ny, nx) FP64 array."""
+    i = lbm_info(sim)
+    out = np.zeros((i["lattice"], i["ny"], i["nx"]))
+    _check(lib().lbm_get_state(sim, _dp(out), out.size))
+    return out
+
+
+def lbm_set_state(sim: int, g: np.ndarray) -> None:
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _check(lib().lbm_set_state(sim, _dp(g), g.size))
+
+
+def lbm_get_labels(sim: int) -> np.ndarray:
+    i = lbm_info(sim)
+    out = np.zeros((i["ny"], i["nx"]), dtype=np.uint8)
+    _check(lib().lbm_get_labels(sim, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), out.size))
+    return out
+
+
+def lbm_set_tile(sim: int, block_x: int, block_y: int) -> None:
+    _check(lib().lbm_set_tile(sim, block_x, block_y))
+
+
+class Simulation:
+    """Owning handle: ``with Simulation(...) as s: lbm_step(s.handle, n)``."""
+
+    def __init__(self, lattice, nx, ny, tau, omega, **geometry):
+        self.geom = make_geometry(**geometry)
+        self.handle = lbm_create(lattice, nx, ny, tau, omega, self.geom)
+
+    def close(self):
+        if self.handle:
+            lbm_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
