@@ -287,9 +287,7 @@ struct lbm_sim {
     int* d_tile_slot = nullptr;
     double2* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
-    long long* d_step = nullptr;
     int* d_err = nullptr;
-    double* d_drive = nullptr;
     double2* d_history = nullptr;
     size_t cap = 0;
     size_t device_bytes = 0;
@@ -334,9 +332,7 @@ void free_sim(lbm_sim* s) {
     cudaFree(s->d_tile_slot);
     cudaFree(s->d_partials);
     cudaFree(s->d_ticket);
-    cudaFree(s->d_step);
     cudaFree(s->d_err);
-    cudaFree(s->d_drive);
     cudaFree(s->d_history);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -365,33 +361,20 @@ int setup_tiles(lbm_sim* s) {
     return LBM_OK;
 }
 
-// Make room for the drive table and force history of `need` steps.
+// Make room for the force history of `need` steps.
 int ensure_capacity(lbm_sim* s, size_t need) {
     if (need <= s->cap) return LBM_OK;
     size_t cap = std::max<size_t>(std::max<size_t>(need, 2 * s->cap), 1024);
-    double* drive = nullptr;
     double2* hist = nullptr;
-    CUDA_TRY(cudaMalloc((void**)&drive, cap * sizeof(double)));
-    if (cudaMalloc((void**)&hist, cap * sizeof(double2)) != cudaSuccess) {
-        cudaFree(drive);
-        return set_error(LBM_ENOMEM, "force history of %zu steps", cap);
-    }
-    std::vector<double> table(cap);
-    for (size_t n = 0; n < cap; ++n) table[n] = drive_value(s->geom.drive, s->geom.u0, s->omega, (long)n);
+    CUDA_TRY(cudaMalloc((void**)&hist, cap * sizeof(double2)));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    CUDA_TRY(cudaMemcpy(drive, table.data(), cap * sizeof(double), cudaMemcpyHostToDevice));
-    s->h2d_bytes += cap * sizeof(double);
     CUDA_TRY(cudaMemset(hist, 0, cap * sizeof(double2)));
     if (s->d_history && s->steps_done > 0)
         CUDA_TRY(cudaMemcpy(hist, s->d_history, (size_t)s->steps_done * sizeof(double2), cudaMemcpyDeviceToDevice));
-    cudaFree(s->d_drive);
     cudaFree(s->d_history);
-    s->device_bytes += (cap - s->cap) * (sizeof(double) + sizeof(double2));
-    s->d_drive = drive;
+    s->device_bytes += (cap - s->cap) * sizeof(double2);
     s->d_history = hist;
     s->cap = cap;
-    s->dev.drive = drive;
-    s->dev.history = hist;
     return LBM_OK;
 }
 
@@ -524,12 +507,10 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     TRY_OR_FREE(dev_alloc(s, &s->d_cls, plane));
     TRY_OR_FREE(dev_alloc(s, &s->d_links, plane));
     TRY_OR_FREE(dev_alloc(s, &s->d_ticket, 1));
-    TRY_OR_FREE(dev_alloc(s, &s->d_step, 1));
     TRY_OR_FREE(dev_alloc(s, &s->d_err, 1));
     if (cudaMemcpy(s->d_cls, cls_p.data(), plane, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(s->d_links, links_p.data(), plane * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(s->d_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(s->d_step, 0, sizeof(long long)) != cudaSuccess ||
         cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
         free_sim(s);
         return set_error(LBM_ECUDA, "upload of geometry failed");
@@ -540,7 +521,6 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.cls = s->d_cls;
     d.links = s->d_links;
     d.ticket = s->d_ticket;
-    d.step = s->d_step;
     d.err = s->d_err;
     d.fconst = make_double2(s->fconst[0], s->fconst[1]);
     d.plane = (long long)plane;
@@ -586,6 +566,8 @@ int lbm_step(lbm_sim* s, long n) {
     for (long k = 0; k < n; ++k) {
         s->dev.src = s->buf[s->cur];
         s->dev.dst = s->buf[s->cur ^ 1];
+        s->dev.dv = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done);
+        s->dev.force_out = s->d_history + s->steps_done;
         const cudaError_t e = s->launch(s->dev, block, s->stream);
         if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;

@@ -5,9 +5,9 @@
 // (Eq. 16), the Hermite equilibrium (Eq. 15 or its 4th-order continuation), the regularized
 // collision (Eqs. 18-19) or the plain BGK step (Eq. 14), an optional body force, and the store.
 // The momentum given to the body by bounce-back is reduced in FP64 (warp shuffles, then a fixed
-// slot per tile); the last tile of an instance to finish sums the slots in a fixed order, appends
-// (Fx, Fy) to the force history and advances the instance's step counter.  No block ever waits
-// for another.
+// slot per tile that holds body links); the last of those tiles to finish sums the slots in a
+// fixed order and writes (Fx, Fy) of the step.  Tiles without body links skip the reduction
+// entirely.  No block ever waits for another.
 //
 // Storage.  Populations are kept as scaled deviations from the rest state,
 //     h_i = (f_i - w_i rho0) / (w_i s),
@@ -40,12 +40,12 @@ struct InstDev {
     const ulonglong2* links;     // [ny][pitch]: .x bit i = link i blocked by the body (label 1),
                                  //              .y bit i = blocked by a static wall (label 2)
     const int* tile_slot;        // [ntiles] force-partial slot of a tile, -1 if it has no body link
-    double2* partials;           // [nslots] per-tile FP64 force partials
-    unsigned int* ticket;        // tiles of the current step that have finished
-    long long* step;             // device step counter n
-    const double* drive;         // [capacity] U_w(n + 1/2) (wall drive) or g(n + 1/2) (body force)
-    double2* history;            // [capacity] force on the body during step n
+    double2* partials;           // [nslots] per-tile FP64 force partials (scratch)
+    unsigned int* ticket;        // slot tiles of the current step that have finished (scratch, 0
+                                 // between launches: the last slot tile resets it)
+    double2* force_out;          // force on the body during this step (written by the last slot tile)
     int* err;                    // bit 0: non-finite force seen
+    double dv;                   // drive of this step: U_w(n + 1/2) (wall) or g(n + 1/2) (body force)
     double2 fconst;              // geometry-only part of the force, -sum c_i 2 w_i rho0
     long long plane;             // ny * pitch
     int nx, ny, pitch;
@@ -238,36 +238,35 @@ __device__ __forceinline__ void node_update(const InstDev& P, int x, int y, int 
     }
 }
 
-// Force partial of a tile (fixed-order reduction), then the last tile of the instance finishes
-// the step: history[n] = sum of slots (fixed order) + constant part, n <- n + 1.
+// Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
+// the slots in a fixed order, adds the constant part and writes the force of the step.
 __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double Fx, double Fy) {
+    const int slot = P.tile_slot[tile];
+    if (slot < 0) return;  // block-uniform: no body link in this tile
     __shared__ double2 red[32];
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nwarps = (blockDim.x * blockDim.y) >> 5;
-    const int slot = P.tile_slot[tile];
-    if (slot >= 0) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        Fx += __shfl_down_sync(0xffffffffu, Fx, o);
+        Fy += __shfl_down_sync(0xffffffffu, Fy, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = make_double2(Fx, Fy);
+    __syncthreads();
+    if (tid < 32) {
+        double2 v = tid < nwarps ? red[tid] : make_double2(0.0, 0.0);
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            Fx += __shfl_down_sync(0xffffffffu, Fx, o);
-            Fy += __shfl_down_sync(0xffffffffu, Fy, o);
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
         }
-        if ((tid & 31) == 0) red[tid >> 5] = make_double2(Fx, Fy);
-        __syncthreads();
-        if (tid < 32) {
-            double2 v = tid < nwarps ? red[tid] : make_double2(0.0, 0.0);
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-                v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-            }
-            if (tid == 0) P.partials[slot] = v;
+        if (tid == 0) {
+            P.partials[slot] = v;
+            __threadfence();
+            const unsigned t = atomicAdd(P.ticket, 1u);
+            last = (t == (unsigned)(P.nslots - 1));
         }
-    }
-    if (tid == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(P.ticket, 1u);
-        last = (t == (unsigned)(P.ntiles - 1));
     }
     __syncthreads();
     if (last && tid < 32) {
@@ -284,12 +283,10 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
             sy += __shfl_down_sync(0xffffffffu, sy, o);
         }
         if (tid == 0) {
-            const long long n = *P.step;
             const double2 F = make_double2(sx + P.fconst.x, sy + P.fconst.y);
             if (!isfinite(F.x) || !isfinite(F.y)) atomicOr(P.err, 1);
-            P.history[n] = F;
+            *P.force_out = F;
             *P.ticket = 0u;
-            *P.step = n + 1;
         }
     }
 }
@@ -300,7 +297,7 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile) {
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
-    const double dv = P.drive[*P.step];
+    const double dv = P.dv;
     double Fx = 0.0, Fy = 0.0;
     const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
     if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, x, y, cls, dv, Fx, Fy);
