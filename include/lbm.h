@@ -162,6 +162,41 @@ int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta);
 int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, int p_min, double* tau,
                               double* omega, int* period);
 
+/*
+ * One time step that allocates no device memory.  (The paper has no counterpart: this is a
+ * service of the library.)
+ *
+ * For callers that cannot call cudaMalloc when they step the solver: code recording its work
+ * into a CUDA graph (no allocation is allowed during stream capture), applications whose device
+ * memory belongs to another allocator that has already reserved it, and loops with a fixed memory
+ * budget where an allocation that may fail or stall is not acceptable.  lbm_step may allocate (it
+ * grows the force history); this call never does, and makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *
+ * It advances the populations in g_in by one step into g_out and writes the force on the body
+ * during the step, (Fx, Fy) in FP64, to force_out[0..1].  All three are device buffers owned by
+ * the caller: g_in and g_out hold Q * ny * pitch values of the simulation's storage type in the
+ * simulation's layout (h_i = (f_i - w_i rho0) / (w_i s), [Q][ny][pitch], pitch and storage from
+ * lbm_info; s = u0 for 16-bit storage, else 1) and must not overlap.  `sim` supplies the geometry,
+ * parameters and tile shape only; its own state and force history are neither read nor changed.
+ * n is the step index: the wall velocity or body force is taken at t = n + 1/2, as in lbm_step.
+ * The work is enqueued on `stream` (a cudaStream_t; 0 is the default stream) and the call returns
+ * before it runs.
+ *
+ * Scratch: the kernel's per-tile force partials and its reduction counter live in one static
+ * device array of the library (LBM_NOALLOC_MAX_SLOTS * 16 + 256 bytes), held by every GPU that
+ * loads the library until the process exits.  A geometry with more than LBM_NOALLOC_MAX_SLOTS
+ * tiles holding body links is rejected with LBM_ERANGE (a larger tile, lbm_set_tile, needs fewer).
+ * All calls in the process share that array: calls whose work overlaps on the GPU (two streams,
+ * or two host threads) race and give wrong forces; serialize them.  The counter is cleared at
+ * the start of every call, so a call that never completed does not affect the next one.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Errors: LBM_EINVAL (null or aliased buffers, n < 0), LBM_ERANGE, LBM_ECUDA.
+ */
+#define LBM_NOALLOC_MAX_SLOTS 8192
+int lbm_step_noalloc(const lbm_sim* sim, long n, const void* g_in, void* g_out, double* force_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -386,6 +386,30 @@ int check_sim(lbm_sim* s) {
 
 }  // namespace
 
+namespace lbm {
+
+// Read-only view of a simulation for other translation units of the library.
+SimView sim_view(const lbm_sim* s) {
+    SimView v;
+    v.device = s->device;
+    v.Q = s->Q;
+    v.storage = s->geom.storage;
+    v.collision = s->geom.collision;
+    v.nx = s->nx;
+    v.ny = s->ny;
+    v.pitch = s->pitch;
+    v.bx = s->bx;
+    v.by = s->by;
+    v.nslots = s->nslots;
+    v.drive = s->geom.drive;
+    v.u0 = s->geom.u0;
+    v.omega = s->omega;
+    v.inst = s->dev;
+    return v;
+}
+
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_last_error(void) { return last_error(); }

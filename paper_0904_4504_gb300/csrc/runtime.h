@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "step_kernel.cuh"
 
 namespace lbm {
 
@@ -31,5 +32,14 @@ void tile_slots(int nx, int ny, int bx, int by, const std::vector<uint64_t>& bod
                 int& ntiles, int& nslots);
 double drive_value(int drive, double u0, double omega, long n);
 int fit_sincos(const double* fx, size_t stride, long n0, long n1, double omega, double coef[3]);
+
+// What another translation unit may read of a simulation: its layout, tile shape and the launch
+// parameters of its step kernel (device pointers to its geometry arrays included).
+struct SimView {
+    int device, Q, storage, collision, nx, ny, pitch, bx, by, nslots, drive;
+    double u0, omega;
+    InstDev inst;
+};
+SimView sim_view(const lbm_sim* s);
 
 }  // namespace lbm

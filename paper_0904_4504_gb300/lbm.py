@@ -110,6 +110,7 @@ def lib():
             "lbm_lattice_velocities": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D]),
             "lbm_params_from_tau_omega": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          _D, _D, ctypes.POINTER(ctypes.c_int)]),
+            "lbm_step_noalloc": (ctypes.c_int, [_P, ctypes.c_long, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -242,6 +243,13 @@ def lbm_get_labels(sim: int) -> np.ndarray:
 
 def lbm_set_tile(sim: int, block_x: int, block_y: int) -> None:
     _check(lib().lbm_set_tile(sim, block_x, block_y))
+
+
+def lbm_step_noalloc(sim: int, n: int, g_in: int, g_out: int, force_out: int, stream=None) -> None:
+    """One step between caller-owned device buffers (raw device addresses, e.g. tensor.data_ptr()),
+    with the force written to force_out (2 doubles); allocates nothing."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().lbm_step_noalloc(sim, n, g_in, g_out, force_out, handle or None))
 
 
 class Simulation:
