@@ -10,6 +10,9 @@ Workloads (synthetic, shaped like the paper's cases):
             lattice step (one fused kernel launch each).
   plate9    D2Q9 plain BGK, FP64: the 4 x 256 oscillating plate (latency-bound correctness case).
   beam2048-<f32|f16|bf16|f64>  D2Q37-H4 beam in a 2048^2 box, tau*omega = 0.1, 1, 10.
+  sweep64[-f16|-bf16]  the batched sweep: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides
+            256..1024) in one batch; a bench step is one batch step of all of them, and runs of
+            --chunk steps are single persistent cooperative launches.
 
 Each rank (torchrun, one per GPU) runs its own replicas: the instances are independent, so the
 work is sharded with no collective on the data path (weak scaling).  One JSON line is printed by
@@ -152,7 +155,110 @@ def lattice_params(L):
     return f
 
 
+def sweep_descs(L, storage):
+    from paper_0904_4504_gb300 import inputs as I
+    out = []
+    for w in I.sweep_d2q37():
+        tau, omega, P = L.lbm_params_from_tau_omega(37, w.tau_omega)
+        out.append((w, L.make_instance(37, w.nx, w.ny, tau, omega, int(w.periods * P), kind=w.geometry, lx=w.lx,
+                                       ly=w.ly, drive=w.drive, u0=w.u0, eq_order=w.eq_order, collision=w.collision,
+                                       storage=storage)))
+    return out
+
+
+def run_batch(args):
+    import torch
+    from paper_0904_4504_gb300 import lbm as L
+    from paper_0904_4504_gb300.builder import build
+
+    rank, world, local = dist_setup(args.gpus)
+    build()
+    storage = STORE[args.workload.split("-")[1]] if "-" in args.workload else STORE["f32"]
+    descs = sweep_descs(L, storage)
+    stream = torch.cuda.Stream()
+    b = L.lbm_batch_create(37, storage, 1)
+    L.lbm_batch_set_stream(b, stream)
+    for _, d in descs:
+        L.lbm_batch_add(b, d)
+    info0 = L.lbm_batch_info(b)
+    fluid, bytes_step = info0["fluid_running"], info0["bytes_per_step"]
+
+    def run(n):
+        left = n
+        while left > 0:
+            k = min(args.chunk, left)
+            L.lbm_batch_run(b, k)
+            left -= k
+
+    run(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = L.lbm_batch_info(b)["launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        run(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    L.lbm_batch_synchronize(b)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, world)
+    info = L.lbm_batch_info(b)
+    launches = info["launches"] - l0
+    assert info["running"] == len(descs), "an instance finished inside the timed region"
+    L.lbm_batch_destroy(b)
+    value = fluid * args.steps * world / (ms_max * 1e-3) / 1e6
+    peak, peak_kind = peaks()
+    achieved = bytes_step * args.steps / (ms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: batch create + 64 x (geometry, upload) -> K steps -> 64 force
+        # histories (D2H) -> 64 fits
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = L.lbm_batch_create(37, storage, 1)
+        slots = [L.lbm_batch_add(b, d) for _, d in descs]
+        run(args.steps)
+        L.lbm_batch_synchronize(b)
+        h2d = d2h = 0
+        for sl in slots:
+            sim = L.lbm_batch_instance(b, sl)
+            d2h += L.lbm_force_history(sim).nbytes
+            h2d += L.lbm_info(sim)["h2d_bytes"]
+        L.lbm_batch_destroy(b)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": fluid * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "scope": "lbm_batch_create + 64 lbm_batch_add (host geometry + upload) -> lbm_batch_run(K) -> "
+                        "64 lbm_force_history"}
+    if rank == 0:
+        line = {
+            "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction of the fused step",
+            "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {v: k for k, v in STORE.items()}[storage], "data": "synthetic",
+            "config": {"workload": args.workload, "instances": len(descs), "lattice": "D2Q37", "eq_order": 4,
+                       "collision": "regularized", "fluid_nodes": fluid, "steps_per_launch": args.chunk,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"]},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": "batch_kernel (persistent, cooperative)",
+                         "bytes_per_batch_step": bytes_step},
+            "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_ours(args):
+    if args.workload.startswith("sweep64"):
+        return run_batch(args)
     import torch
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
@@ -329,6 +435,7 @@ def main():
     ap.add_argument("--workload", default="beam1024")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

@@ -162,6 +162,79 @@ int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta);
 int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, int p_min, double* tau,
                               double* omega, int* period);
 
+/* ----------------------------------------------------------------------------------------------
+ * Batches: many simulations of uneven sizes (a tau*omega and aspect-ratio sweep, or the requests
+ * of a server) advanced together by one persistent kernel.  All instances of a batch share the
+ * lattice, storage type and collision; each has its own grid, geometry, tau, omega, drive and
+ * length in steps.  A run of K steps is one cooperative launch (a node of a CUDA graph built once
+ * per launch shape): its grid fills the GPU, walks the tiles of every unfinished instance and meets
+ * at a grid barrier between steps.  Each barrier wait is bounded (about 2 s by default); a wait
+ * that runs out sets an error flag, the kernel returns, and lbm_batch_synchronize reports
+ * LBM_ETIMEOUT.  Every instance's arithmetic is exactly that of lbm_step on the same instance.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
+
+/* One instance: the arguments of lbm_create plus the number of steps to run. */
+typedef struct {
+    int lattice, nx, ny;
+    double tau, omega;
+    lbm_geometry geom;
+    long nsteps;
+} lbm_instance_desc;
+
+typedef struct {
+    int lattice, storage, collision;
+    int live, running;             /* instances held; instances with steps left                */
+    size_t fluid_running;          /* fluid nodes of the running instances                     */
+    size_t bytes_per_step;         /* algorithmic HBM bytes of one batch step of those          */
+    long long batch_steps, launches;
+    double lattice_updates;        /* fluid-node updates enqueued so far                        */
+    size_t budget_bytes, used_bytes;
+    int max_blocks;                /* co-resident blocks of the cooperative grid                */
+    int uses_graph;                /* 1 if runs are replayed through a CUDA graph               */
+    int block_x, block_y;
+} lbm_batch_info_t;
+
+/* New empty batch on the current device.  device_budget_bytes caps the device memory its instances
+ * may hold (0: free memory at creation minus 1 GiB).  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_create(int lattice, int storage, int collision, size_t device_budget_bytes, lbm_batch** out);
+
+/* Device bytes an instance would hold in a batch (admission by footprint). */
+int lbm_batch_footprint(const lbm_instance_desc* desc, size_t* bytes);
+
+/* Add an instance; it starts at rest with the next run.  *slot receives its index.
+ * LBM_ENOMEM if its footprint does not fit the budget left (nothing is allocated then). */
+int lbm_batch_add(lbm_batch* batch, const lbm_instance_desc* desc, int* slot);
+
+/* Enqueue `steps` batch steps (asynchronous): every instance with steps left advances by up to
+ * `steps`; an instance stops after its own nsteps. */
+int lbm_batch_run(lbm_batch* batch, long steps);
+
+/* Wait for the enqueued runs.  LBM_ETIMEOUT if a barrier wait gave up (the states are then
+ * undefined). */
+int lbm_batch_synchronize(lbm_batch* batch);
+
+/* Steps enqueued for an instance and its length. */
+int lbm_batch_status(lbm_batch* batch, int slot, long* steps_done, long* nsteps);
+
+/* The simulation behind a slot (NULL if none), for lbm_force_history, lbm_fit, lbm_get_state,
+ * lbm_set_state (before the first run) and lbm_info; owned by the batch. */
+lbm_sim* lbm_batch_instance(lbm_batch* batch, int slot);
+
+/* Free an instance's memory (waits for the batch's stream). */
+int lbm_batch_remove(lbm_batch* batch, int slot);
+
+/* Clock cycles a block waits at a grid barrier before giving up (test hook: 0 gives up at once). */
+int lbm_batch_set_barrier_limit(lbm_batch* batch, long long cycles);
+
+int lbm_batch_info(lbm_batch* batch, lbm_batch_info_t* out);
+
+/* Run the batch on `stream` (caller-owned cudaStream_t; 0 is the default stream). */
+int lbm_batch_set_stream(lbm_batch* batch, void* stream);
+
+/* Free the batch and all its instances (waits for its work).  NULL is allowed. */
+void lbm_batch_destroy(lbm_batch* batch);
+
 /*
  * One time step that allocates no device memory.  (The paper has no counterpart: this is a
  * service of the library.)

@@ -34,8 +34,8 @@ static void* find_launcher(int Q, int storage, int coll, bool batched) {
 StepLaunchFn find_step_launcher(int Q, int storage, int coll) {
     return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
 }
-BatchLaunchFn find_batch_launcher(int Q, int storage, int coll) {
-    return reinterpret_cast<BatchLaunchFn>(find_launcher(Q, storage, coll, true));
+BatchKernelFn find_batch_kernel(int Q, int storage, int coll) {
+    return find_launcher(Q, storage, coll, true);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -405,7 +405,21 @@ SimView sim_view(const lbm_sim* s) {
     v.u0 = s->geom.u0;
     v.omega = s->omega;
     v.inst = s->dev;
+    v.buf[0] = s->buf[0];
+    v.buf[1] = s->buf[1];
+    v.cur = s->cur;
+    v.steps_done = s->steps_done;
+    v.history = s->d_history;
+    v.esize = s->esize;
+    v.n_fluid = s->n_fluid;
     return v;
+}
+
+int sim_reserve(lbm_sim* s, size_t steps) { return ensure_capacity(s, steps); }
+
+void sim_advance(lbm_sim* s, long steps) {
+    s->steps_done += steps;
+    s->cur ^= (int)(steps & 1);
 }
 
 }  // namespace lbm

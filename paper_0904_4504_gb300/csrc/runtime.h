@@ -39,7 +39,16 @@ struct SimView {
     int device, Q, storage, collision, nx, ny, pitch, bx, by, nslots, drive;
     double u0, omega;
     InstDev inst;
+    void* buf[2];
+    int cur;
+    long steps_done;
+    double2* history;
+    size_t esize, n_fluid;
 };
 SimView sim_view(const lbm_sim* s);
+// Make room for `steps` entries of force history (may allocate).
+int sim_reserve(lbm_sim* s, size_t steps);
+// Record that `steps` steps were run on the simulation's buffers by another launcher.
+void sim_advance(lbm_sim* s, long steps);
 
 }  // namespace lbm

@@ -87,14 +87,14 @@ template <> struct StoreT<__half> {
 // Advection + bounce-back + collision of the fluid node (x, y).  Adds the momentum the node's
 // blocked body links hand to the body to (Fx, Fy).
 template <class L, class ST, int COLL>
-__device__ __forceinline__ void node_update(const InstDev& P, int x, int y, int cls, double dv, double& Fx,
-                                            double& Fy) {
+__device__ __forceinline__ void node_update(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
+                                            double dv, double& Fx, double& Fy) {
     using S = StoreT<ST>;
     using T = typename S::CT;
     constexpr int Q = L::Q, R = L::R, NP = L::NP;
     constexpr bool SCALED = sizeof(ST) == 2;
-    const ST* __restrict__ src = static_cast<const ST*>(P.src);
-    ST* __restrict__ dst = static_cast<ST*>(P.dst);
+    const ST* __restrict__ src = static_cast<const ST*>(src_v);
+    ST* __restrict__ dst = static_cast<ST*>(dst_v);
     const long long plane = P.plane;
     const int idx = y * P.pitch + x;
 
@@ -240,7 +240,7 @@ __device__ __forceinline__ void node_update(const InstDev& P, int x, int y, int 
 
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
 // the slots in a fixed order, adds the constant part and writes the force of the step.
-__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double Fx, double Fy) {
+__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double2* force_out, double Fx, double Fy) {
     const int slot = P.tile_slot[tile];
     if (slot < 0) return;  // block-uniform: no body link in this tile
     __shared__ double2 red[32];
@@ -285,7 +285,7 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
         if (tid == 0) {
             const double2 F = make_double2(sx + P.fconst.x, sy + P.fconst.y);
             if (!isfinite(F.x) || !isfinite(F.y)) atomicOr(P.err, 1);
-            *P.force_out = F;
+            *force_out = F;
             *P.ticket = 0u;
         }
     }
@@ -293,34 +293,97 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
 
 // One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
 template <class L, class ST, int COLL>
-__device__ __forceinline__ void process_tile(const InstDev& P, int tile) {
+__device__ __forceinline__ void process_tile(const InstDev& P, int tile, const void* src, void* dst, double dv,
+                                             double2* force_out) {
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
-    const double dv = P.dv;
     double Fx = 0.0, Fy = 0.0;
     const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, x, y, cls, dv, Fx, Fy);
-    tile_epilogue(P, tile, Fx, Fy);
+    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, src, dst, x, y, cls, dv, Fx, Fy);
+    tile_epilogue(P, tile, force_out, Fx, Fy);
 }
 
 // Single-instance step: one block per tile.
 template <class L, class ST, int COLL>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
-    process_tile<L, ST, COLL>(P, blockIdx.x);
+    process_tile<L, ST, COLL>(P, blockIdx.x, P.src, P.dst, P.dv, P.force_out);
 }
 
-// Batched step: block b works on tile tiles[b].y of instance tiles[b].x.
+// One instance of a batch: its step-kernel parameters plus what changes from step to step.
+struct BatchInst {
+    InstDev base;                // geometry, constants, force scratch (src/dst/dv/force_out unused)
+    const void* buf[2];          // population buffers; local step n reads buf[n & 1]
+    const double* drive;         // [nsteps] drive of each local step
+    double2* history;            // [nsteps] force of each local step
+    long long start;             // batch step at which local step 0 runs
+    long long nsteps;            // local steps to run
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  Returns false (and sets bit 1 of
+// *err) if this block gave up after `limit` clock cycles; a block that sees the error returns.
+struct GridBarrier {
+    unsigned int* count;         // blocks arrived at the current barrier
+    unsigned int* gen;           // barrier generation
+    int* err;                    // bit 1: a barrier wait timed out
+    long long limit;             // clock cycles a block waits before giving up
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& B) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned int* gen = B.gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        int good = 1;
+        if (atomicAdd(B.count, 1u) == gridDim.x - 1) {
+            *B.count = 0u;
+            __threadfence();
+            atomicAdd(B.gen, 1u);
+        } else {
+            // the clock is checked before the flag, so a limit of 0 gives up at once
+            const long long t0 = clock64();
+            while (true) {
+                if (clock64() - t0 >= B.limit) {
+                    atomicOr(B.err, 2);
+                    good = 0;
+                    break;
+                }
+                if (*gen != g) break;
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (good && (*(volatile int*)B.err & 2)) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Persistent batched step: a cooperative grid walks the tiles of every instance (round robin) for
+// `nsteps` batch steps starting at batch step `step0`, with a grid barrier between steps.
+// Instances outside [start, start + nsteps) at a given step are skipped.
 template <class L, class ST, int COLL>
-__global__ void __launch_bounds__(512) step_kernel_batched(const InstDev* __restrict__ insts,
-                                                           const int2* __restrict__ tiles) {
-    const int2 t = tiles[blockIdx.x];
-    process_tile<L, ST, COLL>(insts[t.x], t.y);
+__global__ void __launch_bounds__(512) batch_kernel(const BatchInst* __restrict__ insts, const int2* __restrict__ tiles,
+                                                    int ntiles, long long step0, int nsteps, GridBarrier bar) {
+    for (int k = 0; k < nsteps; ++k) {
+        const long long gstep = step0 + k;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int2 tl = tiles[t];
+            const BatchInst& B = insts[tl.x];
+            const long long n = gstep - B.start;
+            if (n < 0 || n >= B.nsteps) continue;
+            process_tile<L, ST, COLL>(B.base, tl.y, B.buf[n & 1], const_cast<void*>(B.buf[(n + 1) & 1]),
+                                      B.drive[n], B.history + n);
+        }
+        if (k + 1 < nsteps && !grid_sync(bar)) return;
+    }
 }
 
 using StepLaunchFn = cudaError_t (*)(const InstDev& P, dim3 block, cudaStream_t stream);
-using BatchLaunchFn = cudaError_t (*)(const InstDev* insts, const int2* tiles, int nblocks, dim3 block,
-                                      cudaStream_t stream);
+using BatchKernelFn = const void*;
 
 template <class L, class ST, int COLL>
 cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
@@ -328,15 +391,9 @@ cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-template <class L, class ST, int COLL>
-cudaError_t launch_step_batched(const InstDev* insts, const int2* tiles, int nblocks, dim3 block,
-                                cudaStream_t stream) {
-    step_kernel_batched<L, ST, COLL><<<nblocks, block, 0, stream>>>(insts, tiles);
-    return cudaGetLastError();
-}
-
 // Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.
 StepLaunchFn find_step_launcher(int Q, int storage, int coll);
-BatchLaunchFn find_batch_launcher(int Q, int storage, int coll);
+// Address of batch_kernel<...> for a cooperative launch (nullptr if not built).
+BatchKernelFn find_batch_kernel(int Q, int storage, int coll);
 
 }  // namespace lbm

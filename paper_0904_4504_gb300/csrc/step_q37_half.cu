@@ -5,7 +5,7 @@ namespace lbm {
 
 #define LBM_CASE(ST_ENUM, ST, COLL)                                                            \
     case ST_ENUM * 2 + COLL:                                                                   \
-        return batched ? (void*)&launch_step_batched<D2Q37, ST, COLL> : (void*)&launch_step<D2Q37, ST, COLL>;
+        return batched ? (void*)&batch_kernel<D2Q37, ST, COLL> : (void*)&launch_step<D2Q37, ST, COLL>;
 
 void* find_launcher_q37_half(int storage, int coll, bool batched) {
     switch (storage * 2 + coll) {

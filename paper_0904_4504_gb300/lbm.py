@@ -70,6 +70,31 @@ class lbm_info_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class lbm_instance_desc(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("tau", ctypes.c_double), ("omega", ctypes.c_double),
+        ("geom", lbm_geometry),
+        ("nsteps", ctypes.c_long),
+    ]
+
+
+class lbm_batch_info_t(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int), ("storage", ctypes.c_int), ("collision", ctypes.c_int),
+        ("live", ctypes.c_int), ("running", ctypes.c_int),
+        ("fluid_running", ctypes.c_size_t), ("bytes_per_step", ctypes.c_size_t),
+        ("batch_steps", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+        ("lattice_updates", ctypes.c_double),
+        ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+        ("max_blocks", ctypes.c_int), ("uses_graph", ctypes.c_int),
+        ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -111,6 +136,20 @@ def lib():
             "lbm_params_from_tau_omega": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          _D, _D, ctypes.POINTER(ctypes.c_int)]),
             "lbm_step_noalloc": (ctypes.c_int, [_P, ctypes.c_long, _P, _P, _P, _P]),
+            "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                                ctypes.POINTER(_P)]),
+            "lbm_batch_footprint": (ctypes.c_int, [ctypes.POINTER(lbm_instance_desc), ctypes.POINTER(ctypes.c_size_t)]),
+            "lbm_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(lbm_instance_desc), ctypes.POINTER(ctypes.c_int)]),
+            "lbm_batch_run": (ctypes.c_int, [_P, ctypes.c_long]),
+            "lbm_batch_synchronize": (ctypes.c_int, [_P]),
+            "lbm_batch_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
+                                                ctypes.POINTER(ctypes.c_long)]),
+            "lbm_batch_instance": (_P, [_P, ctypes.c_int]),
+            "lbm_batch_remove": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_batch_set_barrier_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+            "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
+            "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
+            "lbm_batch_destroy": (None, [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -250,6 +289,80 @@ def lbm_step_noalloc(sim: int, n: int, g_in: int, g_out: int, force_out: int, st
     with the force written to force_out (2 doubles); allocates nothing."""
     handle = getattr(stream, "cuda_stream", stream)
     _check(lib().lbm_step_noalloc(sim, n, g_in, g_out, force_out, handle or None))
+
+
+# ------------------------------------------------------------------------------------------------
+# batches
+# ------------------------------------------------------------------------------------------------
+
+def make_instance(lattice, nx, ny, tau, omega, nsteps, **geometry) -> lbm_instance_desc:
+    g = make_geometry(**geometry)
+    d = lbm_instance_desc(lattice, nx, ny, tau, omega, g, nsteps)
+    d._geom_ref = g
+    return d
+
+
+def lbm_batch_create(lattice: int, storage: int, collision: int, device_budget_bytes: int = 0) -> int:
+    h = _P()
+    _check(lib().lbm_batch_create(lattice, storage, collision, device_budget_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def lbm_batch_footprint(desc: lbm_instance_desc) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().lbm_batch_footprint(ctypes.byref(desc), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_batch_add(batch: int, desc: lbm_instance_desc) -> int:
+    slot = ctypes.c_int()
+    _check(lib().lbm_batch_add(batch, ctypes.byref(desc), ctypes.byref(slot)))
+    return slot.value
+
+
+def lbm_batch_run(batch: int, steps: int) -> None:
+    _check(lib().lbm_batch_run(batch, steps))
+
+
+def lbm_batch_synchronize(batch: int) -> None:
+    _check(lib().lbm_batch_synchronize(batch))
+
+
+def lbm_batch_status(batch: int, slot: int):
+    done, total = ctypes.c_long(), ctypes.c_long()
+    _check(lib().lbm_batch_status(batch, slot, ctypes.byref(done), ctypes.byref(total)))
+    return done.value, total.value
+
+
+def lbm_batch_instance(batch: int, slot: int) -> int:
+    h = lib().lbm_batch_instance(batch, slot)
+    if not h:
+        raise LbmError(LBM_ERANGE, f"no instance in slot {slot}")
+    return h
+
+
+def lbm_batch_remove(batch: int, slot: int) -> None:
+    _check(lib().lbm_batch_remove(batch, slot))
+
+
+def lbm_batch_set_barrier_limit(batch: int, cycles: int) -> None:
+    _check(lib().lbm_batch_set_barrier_limit(batch, cycles))
+
+
+def lbm_batch_info(batch: int) -> dict:
+    o = lbm_batch_info_t()
+    _check(lib().lbm_batch_info(batch, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def lbm_batch_set_stream(batch: int, stream=None) -> None:
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().lbm_batch_set_stream(batch, handle or None))
+
+
+def lbm_batch_destroy(batch: int) -> None:
+    if batch:
+        lib().lbm_batch_destroy(batch)
 
 
 class Simulation:

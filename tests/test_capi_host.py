@@ -74,3 +74,18 @@ def test_null_handles_are_rejected():
     assert L.lib().lbm_step(None, 1) == L.LBM_EINVAL
     assert L.lib().lbm_synchronize(None) == L.LBM_EINVAL
     L.lib().lbm_destroy(None)  # NULL-safe
+
+
+def test_batch_footprint_counts_both_population_buffers():
+    d = L.make_instance(37, 1024, 1024, 0.9, 0.05, 3840, kind=L.LBM_GEOM_BEAM, lx=32, ly=32,
+                        storage=L.LBM_STORE_F32)
+    n = L.lbm_batch_footprint(d)
+    assert 2 * 37 * 1024 * 1024 * 4 < n < 2 * 37 * 1024 * 1024 * 4 + 40 * 1024 * 1024
+
+
+def test_batch_create_rejects_bad_arguments():
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_create(11, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+    assert e.value.code == L.LBM_EINVAL
+    assert L.lib().lbm_batch_run(None, 1) == L.LBM_EINVAL
+    L.lib().lbm_batch_destroy(None)

@@ -1,0 +1,179 @@
+"""GPU tests of the batched path: one persistent cooperative kernel over many uneven instances.
+
+An instance's arithmetic in a batch is exactly that of lbm_step on the same instance (same kernel
+body, same tile shape, same fixed-order force reduction), so batch results must equal standalone
+results bit for bit, whatever else shares the launch; and one batch instance is checked against
+the oracle as well.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_0904_4504_gb300 import inputs as I
+from paper_0904_4504_gb300 import lbm as L
+
+from harness import oracle_state_to_g, scaled
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def _desc(Q, nx, ny, tau, omega, nsteps, storage=L.LBM_STORE_F32, coll=L.LBM_COLL_REGULARIZED, **kw):
+    geo = dict(kind=L.LBM_GEOM_BEAM, lx=12, ly=9, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4 if Q == 37 else 2,
+               collision=coll, storage=storage)
+    geo.update(kw)
+    return L.make_instance(Q, nx, ny, tau, omega, nsteps, **geo)
+
+
+def _alone(d):
+    """Run an instance description through the single-instance path."""
+    g = d.geom
+    h = L.lbm_create(d.lattice, d.nx, d.ny, d.tau, d.omega, g)
+    try:
+        L.lbm_step(h, d.nsteps)
+        return L.lbm_get_state(h), L.lbm_force_history(h)
+    finally:
+        L.lbm_destroy(h)
+
+
+MIX = [  # uneven sizes, parameters, geometries and lengths
+    (70, 41, 0.9, 0.05, 37, {}),
+    (133, 64, 1.7, 0.04, 23, dict(lx=20, ly=30)),
+    (96, 96, 0.6, 0.07, 41, dict(kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL)),
+    (45, 200, 3.0, 0.03, 16, dict(lx=8, ly=40, eq_order=2)),
+    (257, 33, 0.75, 0.06, 30, dict(kind=L.LBM_GEOM_NONE)),
+]
+
+
+def test_batch_equals_standalone_bitwise():
+    descs = [_desc(37, nx, ny, tau, om, n, **kw) for nx, ny, tau, om, n, kw in MIX]
+    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+    try:
+        slots = [L.lbm_batch_add(b, d) for d in descs]
+        # uneven chunks; the longest instance needs 41 steps
+        for k in (5, 1, 17, 3, 20):
+            L.lbm_batch_run(b, k)
+        L.lbm_batch_synchronize(b)
+        info = L.lbm_batch_info(b)
+        assert info["running"] == 0 and info["live"] == len(descs)
+        for d, s in zip(descs, slots):
+            done, total = L.lbm_batch_status(b, s)
+            assert done == total == d.nsteps
+            sim = L.lbm_batch_instance(b, s)
+            g_b, F_b = L.lbm_get_state(sim), L.lbm_force_history(sim)
+            g_a, F_a = _alone(d)
+            assert (g_b == g_a).all(), d.nx
+            assert (F_b == F_a).all(), d.nx
+    finally:
+        L.lbm_batch_destroy(b)
+
+
+def test_instances_joining_and_leaving_mid_run():
+    """An instance added after others ran, and another removed while others continue, do not change
+    anyone's result."""
+    d1 = _desc(37, 70, 41, 0.9, 0.05, 30)
+    d2 = _desc(37, 96, 50, 1.3, 0.04, 25, lx=16, ly=16)
+    d3 = _desc(37, 64, 64, 0.7, 0.06, 12, kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL)
+    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+    try:
+        s1 = L.lbm_batch_add(b, d1)
+        s3 = L.lbm_batch_add(b, d3)
+        L.lbm_batch_run(b, 7)
+        s2 = L.lbm_batch_add(b, d2)        # joins at batch step 7
+        L.lbm_batch_run(b, 6)
+        L.lbm_batch_run(b, 9)              # d3 finishes at 12 inside this run
+        L.lbm_batch_synchronize(b)
+        g3 = L.lbm_get_state(L.lbm_batch_instance(b, s3))
+        L.lbm_batch_remove(b, s3)
+        L.lbm_batch_run(b, 40)
+        L.lbm_batch_synchronize(b)
+        for d, s, g_done in ((d1, s1, None), (d2, s2, None), (d3, None, g3)):
+            g_a, F_a = _alone(d)
+            if s is None:
+                assert (g_done == g_a).all()
+                continue
+            sim = L.lbm_batch_instance(b, s)
+            assert (L.lbm_get_state(sim) == g_a).all()
+            assert (L.lbm_force_history(sim) == F_a).all()
+    finally:
+        L.lbm_batch_destroy(b)
+
+
+def test_batch_instance_matches_oracle():
+    Q, nx, ny, tau, omega, n = 37, 70, 41, 0.9, 0.05, 20
+    b = L.lbm_batch_create(Q, L.LBM_STORE_F64, L.LBM_COLL_REGULARIZED)
+    try:
+        s = L.lbm_batch_add(b, _desc(Q, nx, ny, tau, omega, n, storage=L.LBM_STORE_F64))
+        L.lbm_batch_add(b, _desc(Q, 64, 64, 0.7, 0.06, 9, storage=L.LBM_STORE_F64))
+        L.lbm_batch_run(b, n)
+        L.lbm_batch_synchronize(b)
+        sim = L.lbm_batch_instance(b, s)
+        g, F = L.lbm_get_state(sim), L.lbm_force_history(sim)
+    finally:
+        L.lbm_batch_destroy(b)
+    lab = orc.geometry_beam(nx, ny, 12, 9)
+    f, F_or = orc.run(Q, lab, tau, omega, 1e-3, n, eq_order=4, collision=orc.COLL_REG, drive=orc.DRIVE_BODY,
+                      nthreads=orc.max_threads())
+    g_or = oracle_state_to_g(Q, f)
+    fl = lab == 0
+    err = np.abs(scaled(Q, g)[:, fl] - scaled(Q, g_or)[:, fl]).max()
+    assert err <= 2e-13 * n * np.abs(scaled(Q, g_or)[:, fl]).max() + n * 2e-15
+    assert np.abs(F[:, 0] - F_or[:, 0]).max() <= 1e-11 * np.abs(F_or[:, 0]).max()
+
+
+def test_barrier_timeout_is_reported_not_hung():
+    """A barrier wait that runs out (limit 0: give up at once) ends the kernel and is reported."""
+    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+    try:
+        for k in range(3):
+            L.lbm_batch_add(b, _desc(37, 256, 256, 0.9, 0.05, 10))
+        assert L.lbm_batch_info(b)["max_blocks"] > 1
+        L.lbm_batch_set_barrier_limit(b, 0)
+        L.lbm_batch_run(b, 4)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_batch_synchronize(b)
+        assert e.value.code == L.LBM_ETIMEOUT
+    finally:
+        L.lbm_batch_destroy(b)
+    # the context is still usable afterwards
+    h = L.lbm_create(37, 64, 48, 0.9, 0.05, L.make_geometry(kind=L.LBM_GEOM_NONE))
+    L.lbm_step(h, 2)
+    L.lbm_synchronize(h)
+    L.lbm_destroy(h)
+
+
+def test_admission_by_footprint():
+    d = _desc(37, 512, 512, 0.9, 0.05, 100)
+    need = L.lbm_batch_footprint(d)
+    assert need >= 2 * 37 * 512 * 512 * 4
+    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED, int(1.5 * need))
+    try:
+        L.lbm_batch_add(b, d)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_batch_add(b, d)
+        assert e.value.code == L.LBM_ENOMEM
+        assert L.lbm_batch_info(b)["live"] == 1
+    finally:
+        L.lbm_batch_destroy(b)
+
+
+def test_batch_sweep_shapes_run():
+    """The 64-instance sweep (sizes 256..1024, AR 0.25..2) fits and runs a few steps."""
+    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+    try:
+        for w in I.sweep_d2q37():
+            tau, omega, P = orc.params_from_tau_omega(37, w.tau_omega)
+            L.lbm_batch_add(b, L.make_instance(37, w.nx, w.ny, tau, omega, int(w.periods * P), kind=w.geometry,
+                                               lx=w.lx, ly=w.ly, drive=w.drive, u0=w.u0, eq_order=4,
+                                               collision=w.collision, storage=w.storage))
+        L.lbm_batch_run(b, 3)
+        L.lbm_batch_synchronize(b)
+        info = L.lbm_batch_info(b)
+        assert info["live"] == 64 and info["running"] == 64
+    finally:
+        L.lbm_batch_destroy(b)
