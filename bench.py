@@ -3,7 +3,7 @@
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
 Workloads (synthetic, shaped like the paper's cases):
-  beam1024x1  the tau*omega = 1 instance of beam1024 alone (profiling).
+  beam1024x1[-f16|-bf16]  the tau*omega = 1 instance of beam1024 alone (profiling).
   beam1024  D2Q37, 4th-order equilibrium, regularized collision, FP32 storage: a 32 x 32 beam
             section centred in a 1024^2 periodic box, body-frame drive, three instances at
             tau*omega = 0.01, 1, 10 (default).  One bench step advances every instance by one
@@ -44,8 +44,9 @@ def workload_list(name):
     from paper_0904_4504_gb300 import inputs as I
     if name == "beam1024":
         return [I.beam_d2q37_h4(to) for to in I.BEAM_TAU_OMEGAS]
-    if name == "beam1024x1":
-        return [I.beam_d2q37_h4(1.0)]
+    if name.startswith("beam1024x1"):
+        st = STORE[name.split("-")[1]] if "-" in name else STORE["f32"]
+        return [I.beam_d2q37_h4(1.0, storage=st)]
     if name == "plate9":
         return [I.plate_d2q9_fp64()]
     if name.startswith("beam2048-"):
@@ -274,6 +275,8 @@ def run_ours(args):
         L.lbm_set_stream(h, stream)
         if args.tile:
             L.lbm_set_tile(h, *args.tile)
+        if args.variant is not None:
+            L.lbm_set_variant(h, args.variant)
         sims.append(h)
     infos = [L.lbm_info(h) for h in sims]
     fluid = sum(i["n_fluid"] for i in infos)
@@ -340,7 +343,7 @@ def run_ours(args):
                        "nodes_per_instance": [w.nx * w.ny for w in wl], "fluid_nodes": fluid,
                        "l2": "inputs larger than L2 (no flush)" if bytes_step / len(wl) > 2 * 129e6 else
                              "inputs smaller than L2", "parallelism": f"replicas x{world}",
-                       "tile": list(args.tile) if args.tile else [infos[0]["block_x"], infos[0]["block_y"]]},
+                       "tile": [infos[0]["block_x"], infos[0]["block_y"]], "variant": infos[0]["variant"]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": "step_kernel (fused stream+collide+force)",
@@ -435,6 +438,7 @@ def main():
     ap.add_argument("--workload", default="beam1024")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, nargs=2, default=None)
+    ap.add_argument("--variant", type=int, default=None, help="step kernel variant (lbm_set_variant)")
     ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")

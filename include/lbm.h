@@ -142,12 +142,27 @@ typedef struct {
     size_t device_bytes;         /* device memory held by the simulation                          */
     int block_x, block_y;        /* tile shape of the step kernel                                  */
     size_t h2d_bytes, d2h_bytes; /* host<->device bytes copied by the library so far               */
+    int variant;                 /* step kernel in use, see lbm_set_variant                        */
 } lbm_info_t;
 
 int lbm_info(lbm_sim* sim, lbm_info_t* out);
 
-/* Set the step kernel's tile (block_x a multiple of 32, block_x * block_y <= 512). */
+/* Use the plain step kernel (variant 0) with this tile (block_x a multiple of 32,
+ * block_x * block_y <= 512).  Results do not depend on the tile, except for the order in which the
+ * FP64 force partials of the tiles are summed. */
 int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
+
+/* Choose the step kernel.  0: plain kernel, one block per tile of lbm_set_tile's shape, wrapped
+ * global loads (the default).  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
+ * copied to shared memory by bulk tensor copies (TMA), one box per direction plane:
+ * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
+ * 20, 21, 22: two neighbouring nodes per thread (paired loads and stores), tiles of 64 x 4,
+ * 64 x 2 or 128 x 2 nodes (D2Q9: 10 and 20 only).
+ * Every variant evaluates the same expressions in the same order; results agree to FP32 rounding
+ * (the compiler may contract them into different fused multiply-adds in different kernels) and the
+ * force also by the order in which tile partials are summed when the tile shape differs.
+ * LBM_EINVAL if the variant is not built for the simulation's storage type. */
+int lbm_set_variant(lbm_sim* sim, int variant);
 
 /* Velocity table of a lattice in the library's direction order: c_xy[2i], c_xy[2i+1], w[i], theta.
  * Any output may be NULL.  Returns Q, or LBM_EINVAL. */

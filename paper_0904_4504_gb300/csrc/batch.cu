@@ -26,7 +26,7 @@ struct Slot {
     lbm_sim* sim = nullptr;
     long long start = 0;      // batch step of the instance's step 0
     long long nsteps = 0;
-    double* d_drive = nullptr;
+    double* d_drive = nullptr;   // [nsteps] drive, then [nsteps] of it in FP32 (same allocation)
     size_t bytes = 0;
 };
 
@@ -111,7 +111,7 @@ size_t footprint(const HostLattice& H, int nx, int ny, int storage, long nsteps,
     const size_t tiles = (size_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by);
     const size_t hist = std::max<size_t>(1024, (size_t)nsteps);
     return 2 * plane * H.Q * es + plane * (1 + sizeof(ulonglong2)) + tiles * (sizeof(int) + sizeof(double2)) +
-           hist * sizeof(double2) + (size_t)nsteps * sizeof(double) + 4096;
+           hist * sizeof(double2) + (size_t)nsteps * (sizeof(double) + sizeof(float)) + 4096;
 }
 
 // Rebuild the per-instance launch table and the tile list of the unfinished instances.
@@ -129,6 +129,7 @@ int rebuild(lbm_batch* b) {
         I.buf[0] = v.buf[0];
         I.buf[1] = v.buf[1];
         I.drive = s.d_drive;
+        I.drive_f = reinterpret_cast<const float*>(s.d_drive + s.nsteps);
         I.history = v.history;
         I.start = s.start;
         I.nsteps = s.nsteps;
@@ -294,8 +295,14 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     if ((rc = lbm_set_stream(sim, b->stream))) return undo(rc);
     if ((rc = lbm_set_tile(sim, b->bx, b->by))) return undo(rc);
     if ((rc = sim_reserve(sim, (size_t)d->nsteps))) return undo(rc);
-    std::vector<double> table((size_t)d->nsteps);
-    for (long n = 0; n < d->nsteps; ++n) table[(size_t)n] = drive_value(d->geom.drive, d->geom.u0, d->omega, n);
+    // drive table: nsteps doubles followed by the same values as nsteps floats
+    const size_t N = (size_t)d->nsteps;
+    std::vector<double> table(N + (N + 1) / 2, 0.0);
+    float* tf = reinterpret_cast<float*>(table.data() + N);
+    for (size_t n = 0; n < N; ++n) {
+        table[n] = drive_value(d->geom.drive, d->geom.u0, d->omega, (long)n);
+        tf[n] = (float)table[n];
+    }
     double* drv = nullptr;
     if (cudaMalloc((void**)&drv, table.size() * sizeof(double)) != cudaSuccess)
         return undo(set_error(LBM_ENOMEM, "drive table"));

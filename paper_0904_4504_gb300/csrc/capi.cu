@@ -3,6 +3,8 @@
 // The runtime rasterizes the geometry, classifies nodes and blocked links once, owns the device
 // buffers of a simulation, tabulates the drive in FP64, launches the fused step kernel once per
 // time step on the simulation's stream, and reads back the FP64 force history.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,9 +18,72 @@
 
 #include "lbm.h"
 #include "runtime.h"
-#include "step_kernel.cuh"
+#include "step_tma.cuh"
 
 namespace lbm {
+
+void* find_tma_launcher_q9(int storage, int coll, int variant);
+void* find_tma_launcher_q37_wide(int storage, int coll, int variant);
+void* find_tma_launcher_q37_half(int storage, int coll, int variant);
+void tma_box_q9(int storage, int bx, int* bw, int* pad);
+void tma_box_q37_wide(int storage, int bx, int* bw, int* pad);
+void tma_box_q37_half(int storage, int bx, int* bw, int* pad);
+
+static TmaStepLaunchFn find_tma_launcher(int Q, int storage, int coll, int variant) {
+    void* f = nullptr;
+    if (Q == 9) f = find_tma_launcher_q9(storage, coll, variant);
+    else if (Q == 37 && storage == ST_F32) f = find_tma_launcher_q37_wide(storage, coll, variant);
+    else if (Q == 37) f = find_tma_launcher_q37_half(storage, coll, variant);
+    return reinterpret_cast<TmaStepLaunchFn>(f);
+}
+
+// Tile of a staged variant (see lbm_set_variant); false for other variants.
+static bool variant_tile(int variant, int* bx, int* by) {
+    switch (variant) {
+        case 10: *bx = 32; *by = 4; return true;
+        case 11: *bx = 64; *by = 2; return true;
+        case 12: *bx = 64; *by = 4; return true;
+        case 20: *bx = 64; *by = 4; return true;
+        case 21: *bx = 64; *by = 2; return true;
+        case 22: *bx = 128; *by = 2; return true;
+        default: return false;
+    }
+}
+
+static void tma_box(int Q, int storage, int bx, int* bw, int* pad) {
+    *bw = *pad = 0;
+    if (Q == 9) tma_box_q9(storage, bx, bw, pad);
+    else if (Q == 37 && storage == ST_F32) tma_box_q37_wide(storage, bx, bw, pad);
+    else if (Q == 37) tma_box_q37_half(storage, bx, bw, pad);
+}
+
+// Tensor map of one population buffer: 3-D (x, y, direction), boxes of bw x by x 1.
+static int encode_map(CUtensorMap* map, void* base, int storage, int nx, int ny, int Q, int pitch, int bw, int by) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return set_error(LBM_ECUDA, "cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const size_t es = storage_size(storage);
+    CUtensorMapDataType dt = storage == ST_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : storage == ST_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                             : storage == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)Q};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * es * ny};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LBM_OK;
+}
 
 void* find_launcher_q9(int storage, int coll, bool batched);
 void* find_launcher_q37_wide(int storage, int coll, bool batched);
@@ -298,7 +363,11 @@ struct lbm_sim {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int bx = 32, by = 4, ntx = 0, ntiles = 0, nslots = 0;
+    int plain_bx = 32, plain_by = 4;   // tile of the plain kernel (lbm_set_tile)
+    int variant = 0;                   // 0 plain kernel; 2, 3: TMA kernel with that many stages
     StepLaunchFn launch = nullptr;
+    TmaStepLaunchFn tma_launch = nullptr;
+    CUtensorMap maps[2];
     InstDev dev{};
 };
 
@@ -575,6 +644,12 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.reg_a = (1.0 - 1.0 / tau) / (2.0 * H.theta * H.theta);
     d.src_k = (1.0 - 0.5 / tau) / H.theta;
     d.mw_k = 2.0 * g.rho0 / (H.theta * d.s);
+    d.rho0_f = (float)d.rho0;
+    d.s_f = (float)d.s;
+    d.inv_s_f = (float)d.inv_s;
+    d.omega_c_f = (float)d.omega_c;
+    d.reg_a_f = (float)d.reg_a;
+    d.src_k_f = (float)d.src_k;
     TRY_OR_FREE(setup_tiles(s));
     TRY_OR_FREE(ensure_capacity(s, 1024));
     *out = s;
@@ -588,8 +663,30 @@ int lbm_set_tile(lbm_sim* s, int block_x, int block_y) {
         return set_error(LBM_EINVAL, "tile %dx%d: need block_x a multiple of 32 and block_x*block_y <= 512", block_x,
                          block_y);
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    s->bx = block_x;
-    s->by = block_y;
+    s->plain_bx = s->bx = block_x;
+    s->plain_by = s->by = block_y;
+    s->variant = 0;
+    s->tma_launch = nullptr;
+    return setup_tiles(s);
+}
+
+int lbm_set_variant(lbm_sim* s, int variant) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (variant == 0) return lbm_set_tile(s, s->plain_bx, s->plain_by);
+    int bx, by, bw, pad;
+    TmaStepLaunchFn fn = find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
+    if (!fn || !variant_tile(variant, &bx, &by))
+        return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);
+    tma_box(s->Q, s->geom.storage, bx, &bw, &pad);
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < 2; ++k)
+        if ((rc = encode_map(&s->maps[k], s->buf[k], s->geom.storage, s->nx, s->ny, s->Q, s->pitch, bw, by)))
+            return rc;
+    s->bx = bx;
+    s->by = by;
+    s->variant = variant;
+    s->tma_launch = fn;
     return setup_tiles(s);
 }
 
@@ -605,8 +702,10 @@ int lbm_step(lbm_sim* s, long n) {
         s->dev.src = s->buf[s->cur];
         s->dev.dst = s->buf[s->cur ^ 1];
         s->dev.dv = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done);
+        s->dev.dv_f = (float)s->dev.dv;
         s->dev.force_out = s->d_history + s->steps_done;
-        const cudaError_t e = s->launch(s->dev, block, s->stream);
+        const cudaError_t e = s->tma_launch ? s->tma_launch(s->dev, s->maps[s->cur], s->stream)
+                                            : s->launch(s->dev, block, s->stream);
         if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
         ++s->steps_done;
@@ -620,6 +719,7 @@ int lbm_synchronize(lbm_sim* s) {
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     int err = 0;
     CUDA_TRY(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 4) return set_error(LBM_ETIMEOUT, "a bounded wait for staged tile loads timed out");
     if (err & 1) return set_error(LBM_ENONFINITE, "force became non-finite: the run diverged");
     return LBM_OK;
 }
@@ -770,6 +870,7 @@ int lbm_info(lbm_sim* s, lbm_info_t* o) {
     o->block_y = s->by;
     o->h2d_bytes = s->h2d_bytes;
     o->d2h_bytes = s->d2h_bytes;
+    o->variant = s->variant;
     return LBM_OK;
 }
 

@@ -60,45 +60,82 @@ struct InstDev {
     double reg_a;                // (1 - 1/tau) / (2 theta^2)
     double src_k;                // (1 - 1/(2 tau)) / theta
     double mw_k;                 // 2 rho0 / (theta s): moving-wall term per unit c_i.U_w
+    // FP32 copies of the constants above (and of dv), so that FP32 arithmetic converts nothing per
+    // node: double -> float conversions run on the FP64 pipe, which is slow on this GPU
+    float dv_f, rho0_f, s_f, inv_s_f, omega_c_f, reg_a_f, src_k_f, pad_f;
 };
 
+// A launch constant in the arithmetic type T: the double itself, or its FP32 copy.
+template <class T>
+__device__ __forceinline__ T kconst(double d, float f);
+template <>
+__device__ __forceinline__ double kconst<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float kconst<float>(double, float f) { return f; }
+
 template <class ST> struct StoreT;
+// Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
+// elements) with one access.
 template <> struct StoreT<double> {
     using CT = double;
     static __device__ __forceinline__ double ld(const double* p) { return *p; }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+    static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(double* p, double a, double b) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    }
 };
 template <> struct StoreT<float> {
     using CT = float;
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(float* p, float a, float b) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
 };
 template <> struct StoreT<__nv_bfloat16> {
     using CT = float;
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
 };
 template <> struct StoreT<__half> {
     using CT = float;
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void st2(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
 };
 
-// Advection + bounce-back + collision of the fluid node (x, y).  Adds the momentum the node's
-// blocked body links hand to the body to (Fx, Fy).
-template <class L, class ST, int COLL>
-__device__ __forceinline__ void node_update(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
-                                            double dv, double& Fx, double& Fy) {
+// Eq. 17 from global memory: h_i^adv(x) = h_i(x - c_i), periodic in x and y.
+template <class L, class ST>
+__device__ __forceinline__ void gather_global(const InstDev& P, const ST* __restrict__ src, int x, int y,
+                                              typename StoreT<ST>::CT (&h)[L::Q]) {
     using S = StoreT<ST>;
-    using T = typename S::CT;
-    constexpr int Q = L::Q, R = L::R, NP = L::NP;
-    constexpr bool SCALED = sizeof(ST) == 2;
-    const ST* __restrict__ src = static_cast<const ST*>(src_v);
-    ST* __restrict__ dst = static_cast<ST*>(dst_v);
+    constexpr int Q = L::Q, R = L::R;
     const long long plane = P.plane;
-    const int idx = y * P.pitch + x;
-
-    // periodic wrap of the pull sources
     int roff[2 * R + 1], col[2 * R + 1];
 #pragma unroll
     for (int d = -R; d <= R; ++d) {
@@ -111,14 +148,38 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src_v,
         roff[d + R] = ys * P.pitch;
         col[d + R] = xs;
     }
-
-    // Eq. 17: h_i^adv(x) = h_i(x - c_i)
-    T h[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of<L>(i), cy = cy_of<L>(i);
         h[i] = S::ld(src + i * plane + roff[cy + R] + col[cx + R]);
     }
+}
+
+// Per-node coefficients of the collision output: every output is a polynomial in a = c_i.u/theta
+// whose coefficients depend on the node only.
+template <class T>
+struct Coef {
+    T ax, ay;                  // u / theta
+    T c0, e1, e2, o0, o1;      // even part c0 + a^2 (e1 + a^2 e2), odd part a (o0 + o1 a^2)
+    T rxx, rxy, ryy, hf;       // regularized part and first-order force part
+    T kf, inv_s;               // force coefficient, 1/s
+    T om, e0, kfu;             // plain BGK: 1/tau, equilibrium constant, even source constant
+};
+
+// Bounce-back (fix-up of h on blocked links), moments and collision coefficients of the fluid node
+// (x, y) whose pulled populations are in h.  Adds the momentum the node's blocked body links hand
+// to the body to (Fx, Fy).
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
+                                        float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
+                                        Coef<typename StoreT<ST>::CT>& C) {
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    constexpr int Q = L::Q, NP = L::NP;
+    constexpr bool SCALED = sizeof(ST) == 2;
+    const ST* __restrict__ src = static_cast<const ST*>(src_v);
+    const long long plane = P.plane;
+    const int idx = y * P.pitch + x;
 
     // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
     // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
@@ -160,18 +221,19 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src_v,
         if (py) pyy += (T)(w * py * py) * sp;
     }
     if (SCALED) {
-        const T s = (T)P.s;
+        const T s = kconst<T>(P.s, P.s_f);
         m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
     }
     constexpr double TH = L::theta();
     const T th = (T)TH, ith = (T)(1.0 / TH);
     const T drho = m0;
-    const T rho = (T)P.rho0 + drho;
+    const T rho = kconst<T>(P.rho0, P.rho0_f) + drho;
     const T irho = (T)1 / rho;
-    const T Fbx = P.body_force ? rho * (T)dv : (T)0;
+    const T Fbx = P.body_force ? rho * kconst<T>(dv, dv_f) : (T)0;
     const T ux = (jx + (T)0.5 * Fbx) * irho;
     const T uy = jy * irho;
-    const T ax = ux * ith, ay = uy * ith;
+    C.ax = ux * ith;
+    C.ay = uy * ith;
     const T b = (ux * ux + uy * uy) * ith;
 
     // Eq. 15 (+ 4th order): g_i^eq / w_i = E(a^2) + O(a), a = c_i.u/theta
@@ -183,59 +245,106 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src_v,
         o0 -= (T)0.5 * rho * b;
         o1 = rho * (T)(1.0 / 6.0);
     }
+    C.e1 = e1;
+    C.e2 = e2;
+    C.o0 = o0;
+    C.o1 = o1;
     // Guo-type source, even part kf (a c_x - u_x) and odd part c_x * (kf or F/(2 theta))
-    const T kf = (T)P.src_k * Fbx;
+    const T kf = kconst<T>(P.src_k, P.src_k_f) * Fbx;
     const T kfu = -kf * ux;
-    const T inv_s = SCALED ? (T)P.inv_s : (T)1;
-
+    C.kf = kf;
+    C.inv_s = SCALED ? kconst<T>(P.inv_s, P.inv_s_f) : (T)1;
     if (COLL == COLL_REG) {
         // Eq. 19: Pi^ne = Pi - Pi^eq with Pi^eq = rho theta I + rho u u (exact on these lattices)
         const T Pxx = pxx - drho * th - rho * ux * ux;
         const T Pxy = pxy - rho * ux * uy;
         const T Pyy = pyy - drho * th - rho * uy * uy;
-        const T A = (T)P.reg_a;
-        const T rxx = A * Pxx, rxy = (T)2 * A * Pxy, ryy = A * Pyy;
-        const T c0 = e0 - A * th * (Pxx + Pyy) + kfu;
-        const T hf = (T)0.5 * Fbx * ith;   // first-order part: kept J^ne = -F/2 plus the source
-        S::st(dst + idx, c0 * inv_s);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int px = L::px(k), py = L::py(k);
-            T a = 0;
-            if (px) a += (T)px * ax;
-            if (py) a += (T)py * ay;
-            const T a2 = a * a;
-            T E = c0 + a2 * (e1 + a2 * e2);
-            if (px) E += (T)(px * px) * rxx;
-            if (px && py) E += (T)(px * py) * rxy;
-            if (py) E += (T)(py * py) * ryy;
-            if (px) E += a * ((T)px * kf);
-            T O = a * (o0 + o1 * a2);
-            if (px) O += (T)px * hf;
-            // Eq. 18: f = f^eq + (1 - 1/tau) f^ne (+ source)
-            S::st(dst + (1 + 2 * k) * plane + idx, (E + O) * inv_s);
-            S::st(dst + (2 + 2 * k) * plane + idx, (E - O) * inv_s);
-        }
+        const T A = kconst<T>(P.reg_a, P.reg_a_f);
+        C.rxx = A * Pxx;
+        C.rxy = (T)2 * A * Pxy;
+        C.ryy = A * Pyy;
+        C.c0 = e0 - A * th * (Pxx + Pyy) + kfu;
+        C.hf = (T)0.5 * Fbx * ith;   // first-order part: kept J^ne = -F/2 plus the source
     } else {
-        const T om = (T)P.omega_c;
-        S::st(dst + idx, h[0] + om * (e0 * inv_s - h[0]) + kfu * inv_s);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int px = L::px(k), py = L::py(k);
-            T a = 0;
-            if (px) a += (T)px * ax;
-            if (py) a += (T)py * ay;
-            const T a2 = a * a;
-            const T E = e0 + a2 * (e1 + a2 * e2);
-            const T O = a * (o0 + o1 * a2);
-            T Es = kfu, Os = 0;
-            if (px) { Es += a * ((T)px * kf); Os = (T)px * kf; }
-            const T hp = h[1 + 2 * k], hm = h[2 + 2 * k];
-            // Eq. 14 discretized: f - (f - f^eq)/tau + source
-            S::st(dst + (1 + 2 * k) * plane + idx, hp + om * ((E + O) * inv_s - hp) + (Es + Os) * inv_s);
-            S::st(dst + (2 + 2 * k) * plane + idx, hm + om * ((E - O) * inv_s - hm) + (Es - Os) * inv_s);
-        }
+        C.om = kconst<T>(P.omega_c, P.omega_c_f);
+        C.e0 = e0;
+        C.kfu = kfu;
     }
+    if (SCALED) {
+        // outputs are wanted in storage units (divided by s): scale the coefficients once per node
+        const T is = C.inv_s;
+        C.c0 *= is; C.e1 *= is; C.e2 *= is; C.o0 *= is; C.o1 *= is;
+        C.rxx *= is; C.rxy *= is; C.ryy *= is; C.kf *= is; C.hf *= is;
+        C.e0 *= is; C.kfu *= is;
+    }
+}
+
+// Output of the rest direction, in storage units (the coefficients already carry 1/s).
+template <class L, int COLL, class T>
+__device__ __forceinline__ T eval_rest(const Coef<T>& C, T h0) {
+    if (COLL == COLL_REG) return C.c0;
+    return h0 + C.om * (C.e0 - h0) + C.kfu;
+}
+
+// Outputs of pair k (+p_k, -p_k), in storage units; hp, hm are the pulled populations (BGK only).
+template <class L, int COLL, class T>
+__device__ __forceinline__ void eval_pair(const Coef<T>& C, int k, T hp, T hm, T& op, T& omn) {
+    const int px = L::px(k), py = L::py(k);
+    T a = 0;
+    if (px) a += (T)px * C.ax;
+    if (py) a += (T)py * C.ay;
+    const T a2 = a * a;
+    if (COLL == COLL_REG) {
+        T E = C.c0 + a2 * (C.e1 + a2 * C.e2);
+        if (px) E += (T)(px * px) * C.rxx;
+        if (px && py) E += (T)(px * py) * C.rxy;
+        if (py) E += (T)(py * py) * C.ryy;
+        if (px) E += a * ((T)px * C.kf);
+        T O = a * (C.o0 + C.o1 * a2);
+        if (px) O += (T)px * C.hf;
+        // Eq. 18: f = f^eq + (1 - 1/tau) f^ne (+ source)
+        op = E + O;
+        omn = E - O;
+    } else {
+        const T E = C.e0 + a2 * (C.e1 + a2 * C.e2);
+        const T O = a * (C.o0 + C.o1 * a2);
+        T Es = C.kfu, Os = 0;
+        if (px) { Es += a * ((T)px * C.kf); Os = (T)px * C.kf; }
+        // Eq. 14 discretized: f - (f - f^eq)/tau + source
+        op = hp + C.om * ((E + O) - hp) + (Es + Os);
+        omn = hm + C.om * ((E - O) - hm) + (Es - Os);
+    }
+}
+
+// prepare + evaluation + store of one node.
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void collide_store(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
+                                              double dv, float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx,
+                                              double& Fy) {
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    ST* __restrict__ dst = static_cast<ST*>(dst_v);
+    const long long plane = P.plane;
+    const int idx = y * P.pitch + x;
+    Coef<T> C;
+    prepare<L, ST, COLL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
+    S::st(dst + idx, eval_rest<L, COLL, T>(C, h[0]));
+#pragma unroll
+    for (int k = 0; k < L::NP; ++k) {
+        T op, omn;
+        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
+        S::st(dst + (1 + 2 * k) * plane + idx, op);
+        S::st(dst + (2 + 2 * k) * plane + idx, omn);
+    }
+}
+
+// Advection + bounce-back + collision of the fluid node (x, y), sources from global memory.
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void node_update(const InstDev& P, const void* src, void* dst, int x, int y, int cls,
+                                            double dv, float dv_f, double& Fx, double& Fy) {
+    typename StoreT<ST>::CT h[L::Q];
+    gather_global<L, ST>(P, static_cast<const ST*>(src), x, y, h);
+    collide_store<L, ST, COLL>(P, src, dst, x, y, cls, dv, dv_f, h, Fx, Fy);
 }
 
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
@@ -294,20 +403,20 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
 // One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
 template <class L, class ST, int COLL>
 __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const void* src, void* dst, double dv,
-                                             double2* force_out) {
+                                             float dv_f, double2* force_out) {
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
     double Fx = 0.0, Fy = 0.0;
     const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, src, dst, x, y, cls, dv, Fx, Fy);
+    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
     tile_epilogue(P, tile, force_out, Fx, Fy);
 }
 
 // Single-instance step: one block per tile.
 template <class L, class ST, int COLL>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
-    process_tile<L, ST, COLL>(P, blockIdx.x, P.src, P.dst, P.dv, P.force_out);
+    process_tile<L, ST, COLL>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
 // One instance of a batch: its step-kernel parameters plus what changes from step to step.
@@ -315,6 +424,7 @@ struct BatchInst {
     InstDev base;                // geometry, constants, force scratch (src/dst/dv/force_out unused)
     const void* buf[2];          // population buffers; local step n reads buf[n & 1]
     const double* drive;         // [nsteps] drive of each local step
+    const float* drive_f;        // [nsteps] the same in FP32
     double2* history;            // [nsteps] force of each local step
     long long start;             // batch step at which local step 0 runs
     long long nsteps;            // local steps to run
@@ -366,7 +476,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& B) {
 // `nsteps` batch steps starting at batch step `step0`, with a grid barrier between steps.
 // Instances outside [start, start + nsteps) at a given step are skipped.
 template <class L, class ST, int COLL>
-__global__ void __launch_bounds__(512) batch_kernel(const BatchInst* __restrict__ insts, const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(128, 5) batch_kernel(const BatchInst* __restrict__ insts, const int2* __restrict__ tiles,
                                                     int ntiles, long long step0, int nsteps, GridBarrier bar) {
     for (int k = 0; k < nsteps; ++k) {
         const long long gstep = step0 + k;
@@ -376,7 +486,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchInst* __restrict_
             const long long n = gstep - B.start;
             if (n < 0 || n >= B.nsteps) continue;
             process_tile<L, ST, COLL>(B.base, tl.y, B.buf[n & 1], const_cast<void*>(B.buf[(n + 1) & 1]),
-                                      B.drive[n], B.history + n);
+                                      B.drive[n], B.drive_f[n], B.history + n);
         }
         if (k + 1 < nsteps && !grid_sync(bar)) return;
     }

@@ -1,5 +1,5 @@
 // D2Q9 instantiations of the fused step (all storage types, both collisions).
-#include "step_kernel.cuh"
+#include "step_tma.cuh"
 
 namespace lbm {
 
@@ -19,6 +19,61 @@ void* find_launcher_q9(int storage, int coll, bool batched) {
         LBM_CASE(ST_F16, __half, COLL_REG)
         default:
             return nullptr;
+    }
+}
+
+// Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10, 11, 12 = one
+// node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 20, 21, 22 = two nodes per thread on 64 x 4,
+// 64 x 2, 128 x 2 tiles.
+void* find_tma_launcher_q9(int storage, int coll, int variant) {
+    if (variant < 0 || variant >= 32) return nullptr;
+    switch ((storage * 2 + coll) * 32 + variant) {
+        case (ST_F32 * 2 + COLL_BGK) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, float, COLL_BGK, 32, 4>;
+        case (ST_F32 * 2 + COLL_BGK) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, float, COLL_BGK, 32, 4>;
+        case (ST_F32 * 2 + COLL_REG) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, float, COLL_REG, 32, 4>;
+        case (ST_F32 * 2 + COLL_REG) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, float, COLL_REG, 32, 4>;
+        case (ST_BF16 * 2 + COLL_BGK) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, __nv_bfloat16, COLL_BGK, 32, 4>;
+        case (ST_BF16 * 2 + COLL_BGK) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, __nv_bfloat16, COLL_BGK, 32, 4>;
+        case (ST_BF16 * 2 + COLL_REG) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, __nv_bfloat16, COLL_REG, 32, 4>;
+        case (ST_BF16 * 2 + COLL_REG) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, __nv_bfloat16, COLL_REG, 32, 4>;
+        case (ST_F16 * 2 + COLL_BGK) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, __half, COLL_BGK, 32, 4>;
+        case (ST_F16 * 2 + COLL_BGK) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, __half, COLL_BGK, 32, 4>;
+        case (ST_F16 * 2 + COLL_REG) * 32 + 10:
+            return (void*)&launch_step_tma1<D2Q9, __half, COLL_REG, 32, 4>;
+        case (ST_F16 * 2 + COLL_REG) * 32 + 20:
+            return (void*)&launch_step_pair<D2Q9, __half, COLL_REG, 32, 4>;
+        default:
+            return nullptr;
+    }
+}
+
+// Box of the staged kernels for a storage type and tile width bx: width (elements) and left pad.
+void tma_box_q9(int storage, int bx, int* bw, int* pad) {
+    switch (storage) {
+        case ST_F32:
+            *pad = TmaGeom<D2Q9, float, 2>::PAD;
+            *bw = bx + 2 * *pad;
+            return;
+        case ST_BF16:
+            *pad = TmaGeom<D2Q9, __nv_bfloat16, 2>::PAD;
+            *bw = bx + 2 * *pad;
+            return;
+        case ST_F16:
+            *pad = TmaGeom<D2Q9, __half, 2>::PAD;
+            *bw = bx + 2 * *pad;
+            return;
+        default:
+            *bw = *pad = 0;
     }
 }
 

@@ -64,6 +64,7 @@ class lbm_info_t(ctypes.Structure):
         ("bytes_per_step", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
         ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
         ("h2d_bytes", ctypes.c_size_t), ("d2h_bytes", ctypes.c_size_t),
+        ("variant", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -132,6 +133,7 @@ def lib():
             "lbm_get_labels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ubyte), ctypes.c_size_t]),
             "lbm_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_info_t)]),
             "lbm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+            "lbm_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_lattice_velocities": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D]),
             "lbm_params_from_tau_omega": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          _D, _D, ctypes.POINTER(ctypes.c_int)]),
@@ -282,6 +284,10 @@ def lbm_get_labels(sim: int) -> np.ndarray:
 
 def lbm_set_tile(sim: int, block_x: int, block_y: int) -> None:
     _check(lib().lbm_set_tile(sim, block_x, block_y))
+
+
+def lbm_set_variant(sim: int, variant: int) -> None:
+    _check(lib().lbm_set_variant(sim, variant))
 
 
 def lbm_step_noalloc(sim: int, n: int, g_in: int, g_out: int, force_out: int, stream=None) -> None:

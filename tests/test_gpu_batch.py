@@ -31,10 +31,12 @@ def _desc(Q, nx, ny, tau, omega, nsteps, storage=L.LBM_STORE_F32, coll=L.LBM_COL
 
 
 def _alone(d):
-    """Run an instance description through the single-instance path."""
+    """Run an instance description through the single-instance path, with the batch's tile shape
+    (the tile shape fixes the order in which the FP64 force partials are summed)."""
     g = d.geom
     h = L.lbm_create(d.lattice, d.nx, d.ny, d.tau, d.omega, g)
     try:
+        L.lbm_set_tile(h, 32, 4)
         L.lbm_step(h, d.nsteps)
         return L.lbm_get_state(h), L.lbm_force_history(h)
     finally:

@@ -170,21 +170,63 @@ def test_parity_plate_d2q9_fp64_full_config():
     assert np.abs(F_gpu[:, 1] - F_or[:, 1]).max() <= 1e-12 * np.abs(F_or[:, 1]).max()
 
 
-def test_tile_shapes_do_not_change_results():
-    """Tile shape only changes the order of the FP64 force reduction, never the state."""
-    Q, nx, ny = 37, 70, 41
+@pytest.mark.parametrize("storage", [L.LBM_STORE_F32, L.LBM_STORE_F16])
+def test_kernel_variants_and_tiles_do_not_change_results(storage):
+    """Tile shape and kernel variant (plain or TMA-staged) compute the same step: the states agree
+    to FP32 rounding (the compiler may contract the same source into different FMAs in different
+    kernels, and with 16-bit storage two nearby FP32 values can round to neighbouring 16-bit
+    values: one 16-bit ulp, two half-ulps, is allowed on top), the forces to the FP64 reduction order.  The grid has interior (staged)
+    tiles."""
+    Q, nx, ny = 37, 200, 90
     outs = []
-    for tile in [(32, 8), (64, 4), (128, 1), (32, 16)]:
-        geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=12, ly=9, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
-                               storage=L.LBM_STORE_F32)
+    configs = [("tile", (32, 8)), ("tile", (64, 4)), ("tile", (128, 1)), ("tile", (32, 16)),
+               ("variant", 10), ("variant", 11), ("variant", 12), ("variant", 20), ("variant", 21), ("variant", 22)]
+    for kind, arg in configs:
+        geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
+                               storage=storage)
         h = L.lbm_create(Q, nx, ny, 0.9, 0.05, geom)
-        L.lbm_set_tile(h, *tile)
+        if kind == "tile":
+            L.lbm_set_tile(h, *arg)
+        else:
+            L.lbm_set_variant(h, arg)
+            assert L.lbm_info(h)["variant"] == arg
         L.lbm_step(h, 15)
         outs.append((L.lbm_get_state(h), L.lbm_force_history(h)))
         L.lbm_destroy(h)
-    for g, F in outs[1:]:
-        assert (g == outs[0][0]).all()
-        assert np.abs(F - outs[0][1]).max() <= 1e-15 * np.abs(outs[0][1]).max() + 1e-300
+    h_ref = scaled(Q, outs[0][0])
+    scale = np.abs(h_ref).max()
+    for (kind, arg), (g, F) in zip(configs[1:], outs[1:]):
+        h = scaled(Q, g)
+        err = np.abs(h - h_ref)
+        bound = EPS_STEP[storage] * scale + 2.0 * ROUND16.get(storage, 0.0) * np.maximum(np.abs(h_ref), np.abs(h))
+        assert (err <= bound).all(), (kind, arg, err.max())
+        Ftol = (EPS_STEP[storage] + ROUND16.get(storage, 0.0)) * (np.abs(outs[0][1]).max() + 1.0)
+        assert np.abs(F - outs[0][1]).max() <= Ftol, (kind, arg)
+
+
+@pytest.mark.parametrize("variant", [10, 11, 12, 20, 21, 22])
+def test_parity_staged_variants(variant):
+    """The TMA-staged kernels against the oracle on a grid with interior tiles, FP32."""
+    Q, nx, ny, steps = 37, 200, 90, 12
+    geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=2e-3, eq_order=4,
+                           storage=L.LBM_STORE_F32)
+    lab = orc.geometry_beam(nx, ny, 24, 19)
+    _, w, _ = L.lbm_lattice_velocities(Q)
+    h0 = I.random_scaled_state(Q, nx, ny, -17, 9)
+    h0[:, lab != 0] = 0.0
+    g0 = h0 * w[:, None, None]
+    h = L.lbm_create(Q, nx, ny, 0.9, 0.05, geom)
+    try:
+        L.lbm_set_variant(h, variant)
+        L.lbm_set_state(h, g0)
+        L.lbm_step(h, steps)
+        g, F = L.lbm_get_state(h), L.lbm_force_history(h)
+    finally:
+        L.lbm_destroy(h)
+    f, F_or = orc.run(Q, lab, 0.9, 0.05, 2e-3, steps, eq_order=4, collision=orc.COLL_REG, drive=orc.DRIVE_BODY,
+                      f=g_to_oracle_state(Q, g0), nthreads=orc.max_threads())
+    assert_state_close(Q, g, oracle_state_to_g(Q, f), lab, L.LBM_STORE_F32, steps, g0)
+    assert_force_close(F, F_or, Q, lab, L.LBM_STORE_F32, steps)
 
 
 def test_repeat_runs_are_bitwise_identical():
