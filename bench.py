@@ -10,6 +10,12 @@ Workloads (synthetic, shaped like the paper's cases):
             lattice step (one fused kernel launch each).
   plate9    D2Q9 plain BGK, FP64: the 4 x 256 oscillating plate (latency-bound correctness case).
   beam2048-<f32|f16|bf16|f64>  D2Q37-H4 beam in a 2048^2 box, tau*omega = 0.1, 1, 10.
+  serve[-f16]  the serving loop: the first --requests requests of the seeded request stream (plate
+            or beam, AR 0.25..4, tau*omega 1e-3..1e3, sides 128..2048, 10..50 periods, D2Q9 or
+            D2Q37), submitted at Poisson arrival times; --load sets the offered load as a fraction of
+            the GPU's capacity (estimated from the requests' algorithmic bytes at 0.8 of the measured
+            HBM bandwidth), 0 submits at the stream's own rate (50 per second).  Reports aggregate
+            MLUPS and p50/p99 latency (submit -> fit available).
   sweep64[-f16|-bf16]  the batched sweep: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides
             256..1024) in one batch; a bench step is one batch step of all of them, and runs of
             --chunk steps are single persistent cooperative launches.
@@ -257,7 +263,83 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    import torch
+    from paper_0904_4504_gb300 import inputs as I
+    from paper_0904_4504_gb300 import lbm as L
+    from paper_0904_4504_gb300.builder import build
+
+    rank, world, local = dist_setup(args.gpus)
+    build()
+    storage = STORE["f16"] if args.workload.endswith("-f16") else STORE["f32"]
+    stream = I.serving_requests()[rank * args.requests:(rank + 1) * args.requests]
+    reqs, gpu_s = [], []
+    peak, peak_kind = peaks()
+    for r in stream:
+        w = r.workload
+        tau, omega, P = L.lbm_params_from_tau_omega(w.lattice, w.tau_omega)
+        nsteps = int(round(w.periods * P))
+        d = L.make_instance(w.lattice, w.nx, w.ny, tau, omega, nsteps, kind=w.geometry, lx=w.lx, ly=w.ly,
+                            drive=w.drive, u0=w.u0, eq_order=w.eq_order, collision=w.collision, storage=storage)
+        perim = 2.0 * (w.lx + w.ly) if w.geometry == 1 else float(w.nx)
+        reqs.append((r.arrival_s, L.make_request(d, w.periods / 2.0, perim)))
+        bytes_lu = 2 * w.lattice * L.STORAGE_BYTES[storage]
+        gpu_s.append(w.nx * w.ny * nsteps * bytes_lu / (0.8 * peak * 1e9))
+    if args.load > 0:   # rescale the arrival process to the requested offered load
+        rate = args.load / (sum(gpu_s) / len(gpu_s))
+        arrivals = np.cumsum(np.random.default_rng(I.SERVE_SEED + 1).exponential(1.0 / rate, len(reqs)))
+    else:
+        arrivals = np.array([a for a, _ in reqs]) - reqs[0][0]
+    srv = L.lbm_server_create(0, args.chunk)
+    ids = []
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for (_, rq), at in zip(reqs, arrivals):
+            dt = at - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(L.lbm_server_submit(srv, rq))
+        results = []
+        for i in ids:
+            done, res = L.lbm_server_wait(srv, i, 3600.0)
+            results.append(res)
+        makespan = time.perf_counter() - t0
+    stats = L.lbm_server_stats(srv)
+    L.lbm_server_destroy(srv)
+    barrier(world)
+    lat = np.array([r["done_s"] - r["submit_s"] for r in results])
+    ok = all(r["status"] == 2 for r in results)
+    lu = sum(r["steps"] * r["fluid_nodes"] for r in results)
+    span = max_over_ranks(makespan, world)
+    value = lu * world / span / 1e6
+    if rank == 0:
+        print(json.dumps({
+            "metric": "aggregate MLUPS of the served requests (fluid lattice updates per second, submit of the first "
+                      "to completion of the last) and p50/p99 latency",
+            "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": stats["rounds"], "warmup": 0,
+            "ms_per_step": round(span * 1e3 / max(1, stats["rounds"]), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {v: k for k, v in STORE.items()}[storage],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "requests": len(reqs), "offered_load": args.load or "as generated",
+                       "steps_per_round": args.chunk, "parallelism": f"replicas x{world}"},
+            "latency": {"p50_s": round(float(np.percentile(lat, 50)), 4),
+                        "p99_s": round(float(np.percentile(lat, 99)), 4), "mean_s": round(float(lat.mean()), 4),
+                        "max_s": round(float(lat.max()), 4)},
+            "server": {"completed": stats["completed"], "all_ok": ok, "busy_frac": round(stats["busy_s"] / span, 4),
+                       "peak_running": stats["peak_running"], "peak_used_gb": round(stats["peak_used_bytes"] / 1e9, 3),
+                       "total_lattice_updates": lu, "makespan_s": round(span, 3)},
+            "clocks": clocks.summary(), "gpu_launches": None, "cpu_baseline": None,
+        }), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_ours(args):
+    if args.workload.startswith("serve"):
+        return run_serve(args)
     if args.workload.startswith("sweep64"):
         return run_batch(args)
     import torch
@@ -439,7 +521,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, nargs=2, default=None)
     ap.add_argument("--variant", type=int, default=None, help="step kernel variant (lbm_set_variant)")
-    ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64)")
+    ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64, serve)")
+    ap.add_argument("--requests", type=int, default=48, help="requests per rank (serve)")
+    ap.add_argument("--load", type=float, default=0.7, help="offered load, fraction of capacity (serve; 0: as generated)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

@@ -250,6 +250,70 @@ int lbm_batch_set_stream(lbm_batch* batch, void* stream);
 /* Free the batch and all its instances (waits for its work).  NULL is allowed. */
 void lbm_batch_destroy(lbm_batch* batch);
 
+/* ----------------------------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Clients submit solves (an instance, its
+ * length and how to fit it) from any thread; a worker thread admits them in arrival order as soon
+ * as their device footprint fits the budget, runs all admitted instances of a lattice/storage/
+ * collision class together in the batch kernel (K steps per round; requests that arrive during a
+ * round join the next one), and retires each instance when it has run all its steps: FP64 fit of
+ * its force history (lbm_fit), normalized damping (lbm_gamma_bar), device memory freed.  An
+ * instance's result is the same whether it ran alone or among others (the batch kernel computes
+ * each instance exactly as lbm_step does).  Times are seconds on the host's steady clock since
+ * lbm_server_create.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct lbm_server lbm_server; /* opaque; owned by the library */
+
+typedef struct {
+    lbm_instance_desc desc;   /* the solve; plate, beam or open geometries (not masks)              */
+    double skip_periods;      /* fit window: the steps after this many periods (lbm_fit)           */
+    double perimeter;         /* wetted perimeter for gamma_bar (0: not computed)                  */
+} lbm_request;
+
+typedef struct {
+    long long id;
+    int status;               /* 0 waiting, 1 running, 2 done, negative: LBM_E* failure            */
+    double submit_s, admit_s, done_s;
+    double f_in, f_q, f_0;    /* lbm_fit of the force history                                      */
+    double gamma_bar;
+    long steps;
+    size_t fluid_nodes;
+} lbm_result;
+
+typedef struct {
+    long long submitted, completed, rounds;
+    double lattice_updates;   /* fluid-node updates of the completed requests                      */
+    double busy_s;            /* time with batch work in flight                                    */
+    double elapsed_s;
+    size_t budget_bytes, used_bytes, peak_used_bytes;
+    int peak_running;         /* most instances resident at once                                   */
+    int worker_error;         /* last error of the worker (0 if none)                              */
+} lbm_server_stats_t;
+
+/* Start a server on the current device.  device_budget_bytes caps the memory its instances hold
+ * (0: free memory minus 2 GiB); steps_per_round is K. */
+int lbm_server_create(size_t device_budget_bytes, int steps_per_round, lbm_server** out);
+
+/* Queue a request (returns at once).  LBM_ENOMEM if it could never fit the budget. */
+int lbm_server_submit(lbm_server* server, const lbm_request* req, long long* id);
+
+/* Copy a request's result; returns 1 when it has finished (done or failed), 0 otherwise. */
+int lbm_server_poll(lbm_server* server, long long id, lbm_result* out);
+
+/* Wait up to timeout_s seconds for a request to finish; returns as lbm_server_poll. */
+int lbm_server_wait(lbm_server* server, long long id, double timeout_s, lbm_result* out);
+
+/* Force history of a completed request (as lbm_force_history); kept until released. */
+int lbm_server_force_history(lbm_server* server, long long id, double* out_xy, size_t cap_steps, size_t* n_steps);
+
+/* Forget a finished request. */
+int lbm_server_release(lbm_server* server, long long id);
+
+int lbm_server_stats(lbm_server* server, lbm_server_stats_t* out);
+
+/* Stop the worker (running requests finish their current round and are marked failed), free
+ * everything.  NULL is allowed. */
+void lbm_server_destroy(lbm_server* server);
+
 /*
  * One time step that allocates no device memory.  (The paper has no counterpart: this is a
  * service of the library.)

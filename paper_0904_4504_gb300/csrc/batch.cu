@@ -292,9 +292,11 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
         lbm_destroy(sim);
         return code;
     };
-    if ((rc = lbm_set_stream(sim, b->stream))) return undo(rc);
+    // tile and history first, on the instance's own stream, so that adding an instance does not
+    // wait for a run of the batch that may be in flight
     if ((rc = lbm_set_tile(sim, b->bx, b->by))) return undo(rc);
     if ((rc = sim_reserve(sim, (size_t)d->nsteps))) return undo(rc);
+    if ((rc = lbm_set_stream(sim, b->stream))) return undo(rc);
     // drive table: nsteps doubles followed by the same values as nsteps floats
     const size_t N = (size_t)d->nsteps;
     std::vector<double> table(N + (N + 1) / 2, 0.0);

@@ -96,6 +96,34 @@ class lbm_batch_info_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class lbm_request(ctypes.Structure):
+    _fields_ = [("desc", lbm_instance_desc), ("skip_periods", ctypes.c_double), ("perimeter", ctypes.c_double)]
+
+
+class lbm_result(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_longlong), ("status", ctypes.c_int),
+        ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+        ("f_in", ctypes.c_double), ("f_q", ctypes.c_double), ("f_0", ctypes.c_double),
+        ("gamma_bar", ctypes.c_double), ("steps", ctypes.c_long), ("fluid_nodes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class lbm_server_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+        ("lattice_updates", ctypes.c_double), ("busy_s", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+        ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t), ("peak_used_bytes", ctypes.c_size_t),
+        ("peak_running", ctypes.c_int), ("worker_error", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -152,6 +180,15 @@ def lib():
             "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
             "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
             "lbm_batch_destroy": (None, [_P]),
+            "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
+            "lbm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(lbm_result)]),
+            "lbm_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(lbm_result)]),
+            "lbm_server_force_history": (ctypes.c_int, [_P, ctypes.c_longlong, _D, ctypes.c_size_t,
+                                                        ctypes.POINTER(ctypes.c_size_t)]),
+            "lbm_server_release": (ctypes.c_int, [_P, ctypes.c_longlong]),
+            "lbm_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(lbm_server_stats_t)]),
+            "lbm_server_destroy": (None, [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -369,6 +406,64 @@ def lbm_batch_set_stream(batch: int, stream=None) -> None:
 def lbm_batch_destroy(batch: int) -> None:
     if batch:
         lib().lbm_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------------------------------------
+# serving
+# ------------------------------------------------------------------------------------------------
+
+def lbm_server_create(device_budget_bytes: int = 0, steps_per_round: int = 64) -> int:
+    h = _P()
+    _check(lib().lbm_server_create(device_budget_bytes, steps_per_round, ctypes.byref(h)))
+    return h.value
+
+
+def make_request(desc: lbm_instance_desc, skip_periods: float, perimeter: float = 0.0) -> lbm_request:
+    r = lbm_request(desc, skip_periods, perimeter)
+    r._desc_ref = desc
+    return r
+
+
+def lbm_server_submit(server: int, req: lbm_request) -> int:
+    i = ctypes.c_longlong()
+    _check(lib().lbm_server_submit(server, ctypes.byref(req), ctypes.byref(i)))
+    return i.value
+
+
+def lbm_server_poll(server: int, rid: int):
+    """(finished, result dict)."""
+    r = lbm_result()
+    done = _check(lib().lbm_server_poll(server, rid, ctypes.byref(r)))
+    return bool(done), r.as_dict()
+
+
+def lbm_server_wait(server: int, rid: int, timeout_s: float = 60.0):
+    r = lbm_result()
+    done = _check(lib().lbm_server_wait(server, rid, timeout_s, ctypes.byref(r)))
+    return bool(done), r.as_dict()
+
+
+def lbm_server_force_history(server: int, rid: int) -> np.ndarray:
+    n = ctypes.c_size_t()
+    _check(lib().lbm_server_force_history(server, rid, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 2))
+    _check(lib().lbm_server_force_history(server, rid, _dp(out), n.value, ctypes.byref(n)))
+    return out
+
+
+def lbm_server_release(server: int, rid: int) -> None:
+    _check(lib().lbm_server_release(server, rid))
+
+
+def lbm_server_stats(server: int) -> dict:
+    o = lbm_server_stats_t()
+    _check(lib().lbm_server_stats(server, ctypes.byref(o)))
+    return o.as_dict()
+
+
+def lbm_server_destroy(server: int) -> None:
+    if server:
+        lib().lbm_server_destroy(server)
 
 
 class Simulation:

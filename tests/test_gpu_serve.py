@@ -1,0 +1,105 @@
+"""GPU tests of the serving loop (continuous batching over the batch kernel).
+
+The isolation test is the serving contract: every request gives the same force history and fit
+whether it is served alone or in a mix of requests that arrive at different times, share the GPU
+with other lattices and sizes, and join or leave the batch while it runs.  The batch kernel
+computes each instance exactly as alone, so the histories must be bit for bit equal (the stated
+tolerance is 0).
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_0904_4504_gb300 import lbm as L
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def _req(Q, nx, ny, tau, omega, nsteps, skip=0.25, **kw):
+    geo = dict(kind=L.LBM_GEOM_BEAM, lx=12, ly=9, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3,
+               eq_order=4 if Q == 37 else 2, collision=L.LBM_COLL_REGULARIZED, storage=L.LBM_STORE_F32)
+    geo.update(kw)
+    d = L.make_instance(Q, nx, ny, tau, omega, nsteps, **geo)
+    return L.make_request(d, skip, 2.0 * (geo["lx"] + geo["ly"]) if geo["kind"] == L.LBM_GEOM_BEAM else 0.0)
+
+
+REQS = [
+    (37, 70, 41, 0.9, 0.05, 260, {}),
+    (9, 64, 80, 0.8, 0.06, 300, dict(kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL)),
+    (37, 133, 64, 1.7, 0.04, 200, dict(lx=20, ly=30)),
+    (37, 96, 96, 0.6, 0.07, 150, dict(kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL)),
+    (9, 120, 50, 1.2, 0.05, 280, dict(lx=16, ly=8)),
+    (37, 200, 90, 3.0, 0.03, 300, dict(lx=24, ly=19, storage=L.LBM_STORE_F16)),
+]
+
+
+def _serve(reqs, delays, budget=0, k=16):
+    srv = L.lbm_server_create(budget, k)
+    try:
+        ids = []
+        for r, dly in zip(reqs, delays):
+            time.sleep(dly)
+            ids.append(L.lbm_server_submit(srv, r))
+        out = []
+        for i in ids:
+            done, res = L.lbm_server_wait(srv, i, 120.0)
+            assert done and res["status"] == 2, res
+            out.append((res, L.lbm_server_force_history(srv, i)))
+        stats = L.lbm_server_stats(srv)
+    finally:
+        L.lbm_server_destroy(srv)
+    return out, stats
+
+
+def test_served_result_is_the_same_alone_and_in_the_mix():
+    reqs = [_req(Q, nx, ny, tau, om, n, **kw) for Q, nx, ny, tau, om, n, kw in REQS]
+    mixed, stats = _serve(reqs, [0.0, 0.0, 0.01, 0.0, 0.02, 0.0])
+    assert stats["completed"] == len(reqs) and stats["peak_running"] >= 2
+    for r, (res_m, hist_m) in zip(reqs, mixed):
+        (res_a, hist_a), = _serve([r], [0.0])[0]
+        assert hist_m.shape == hist_a.shape == (r.desc.nsteps, 2)
+        assert (hist_m == hist_a).all()
+        for key in ("f_in", "f_q", "f_0", "gamma_bar"):
+            assert res_m[key] == res_a[key], key
+        assert res_m["admit_s"] >= res_m["submit_s"] and res_m["done_s"] >= res_m["admit_s"]
+
+
+def test_served_fit_matches_direct_fit():
+    r = _req(37, 70, 41, 0.9, 0.05, 400, skip=2.0)
+    (res, hist), = _serve([r], [0.0])[0]
+    h = L.lbm_create(37, 70, 41, 0.9, 0.05, r.desc.geom)
+    try:
+        L.lbm_set_tile(h, 32, 4)
+        L.lbm_step(h, 400)
+        F = L.lbm_force_history(h)
+        f_in, f_q, f_0 = L.lbm_fit(h, 2.0)
+    finally:
+        L.lbm_destroy(h)
+    assert (F == hist).all()
+    assert (res["f_in"], res["f_q"], res["f_0"]) == (f_in, f_q, f_0)
+
+
+def test_admission_waits_for_memory_in_arrival_order():
+    reqs = [_req(37, 256, 256, 0.9, 0.05, 200) for _ in range(3)]
+    need = L.lbm_batch_footprint(reqs[0].desc)
+    out, stats = _serve(reqs, [0.0, 0.0, 0.0], budget=int(1.5 * need), k=32)
+    assert stats["peak_running"] == 1 and stats["completed"] == 3
+    admits = [res["admit_s"] for res, _ in out]
+    dones = [res["done_s"] for res, _ in out]
+    assert admits == sorted(admits)
+    assert admits[1] >= dones[0] and admits[2] >= dones[1]
+
+
+def test_request_larger_than_budget_is_rejected():
+    srv = L.lbm_server_create(1 << 20, 16)
+    try:
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_server_submit(srv, _req(37, 256, 256, 0.9, 0.05, 50))
+        assert e.value.code == L.LBM_ENOMEM
+    finally:
+        L.lbm_server_destroy(srv)
