@@ -16,6 +16,8 @@ Workloads (synthetic, shaped like the paper's cases):
             the GPU's capacity (estimated from the requests' algorithmic bytes at 0.8 of the measured
             HBM bandwidth), 0 submits at the stream's own rate (50 per second).  Reports aggregate
             MLUPS and p50/p99 latency (submit -> fit available).
+  precision2048  precision study: the 2048^2 beam in FP64/FP32/FP16/BF16 storage, force errors
+            against the FP64-storage run and MLUPS of each (prints its own JSON line).
   sweep64[-f16|-bf16]  the batched sweep: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides
             256..1024) in one batch; a bench step is one batch step of all of them, and runs of
             --chunk steps are single persistent cooperative launches.
@@ -173,17 +175,19 @@ def sweep_descs(L, storage):
     return out
 
 
-def run_batch(args):
+def run_batch(args, sub=False):
     import torch
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
 
-    rank, world, local = dist_setup(args.gpus)
+    rank, world, local = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+                          int(os.environ.get("LOCAL_RANK", "0"))) if sub else dist_setup(args.gpus)
     build()
     storage = STORE[args.workload.split("-")[1]] if "-" in args.workload else STORE["f32"]
-    descs = sweep_descs(L, storage)
+    descs = sweep_descs(L, storage)[:args.instances or None]
     stream = torch.cuda.Stream()
     b = L.lbm_batch_create(37, storage, 1)
+    L.lbm_batch_set_mode(b, args.batch_mode)
     L.lbm_batch_set_stream(b, stream)
     for _, d in descs:
         L.lbm_batch_add(b, d)
@@ -227,6 +231,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b = L.lbm_batch_create(37, storage, 1)
+        L.lbm_batch_set_mode(b, args.batch_mode)
         slots = [L.lbm_batch_add(b, d) for _, d in descs]
         run(args.steps)
         L.lbm_batch_synchronize(b)
@@ -250,26 +255,32 @@ def run_batch(args):
             "config": {"workload": args.workload, "instances": len(descs), "lattice": "D2Q37", "eq_order": 4,
                        "collision": "regularized", "fluid_nodes": fluid, "steps_per_launch": args.chunk,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "batch_mode": "persistent" if info["mode"] == 1 else "streams",
                        "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
-                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": "batch_kernel (persistent, cooperative)",
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "batch_kernel (persistent, cooperative)" if info["mode"] == 1 else
+                                   "step kernels of every instance on parallel streams",
                          "bytes_per_batch_step": bytes_step},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": None,
         }
+        if sub:
+            return line
         print(json.dumps(line), flush=True)
-    if world > 1:
+    if world > 1 and not sub:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def run_serve(args):
+def run_serve(args, sub=False):
     import torch
     from paper_0904_4504_gb300 import inputs as I
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
 
-    rank, world, local = dist_setup(args.gpus)
+    rank, world, local = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+                          int(os.environ.get("LOCAL_RANK", "0"))) if sub else dist_setup(args.gpus)
     build()
     storage = STORE["f16"] if args.workload.endswith("-f16") else STORE["f32"]
     stream = I.serving_requests()[rank * args.requests:(rank + 1) * args.requests]
@@ -315,7 +326,7 @@ def run_serve(args):
     span = max_over_ranks(makespan, world)
     value = lu * world / span / 1e6
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": "aggregate MLUPS of the served requests (fluid lattice updates per second, submit of the first "
                       "to completion of the last) and p50/p99 latency",
             "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": stats["rounds"], "warmup": 0,
@@ -331,13 +342,65 @@ def run_serve(args):
                        "peak_running": stats["peak_running"], "peak_used_gb": round(stats["peak_used_bytes"] / 1e9, 3),
                        "total_lattice_updates": lu, "makespan_s": round(span, 3)},
             "clocks": clocks.summary(), "gpu_launches": None, "cpu_baseline": None,
-        }), flush=True)
-    if world > 1:
+        }
+        if sub:
+            return line
+        print(json.dumps(line), flush=True)
+    if world > 1 and not sub:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
+def run_precision(args):
+    """Precision study at full size: the D2Q37-H4 beam in 2048^2 at tau*omega = 0.1, 1, 10 for 30
+    periods in every storage type; in-phase/quadrature force error of each against the FP64-storage
+    run (the FP64 oracle comparison on the 256^2 downscale is tests/test_gpu_precision.py)."""
+    import torch
+    from paper_0904_4504_gb300 import inputs as I
+    from paper_0904_4504_gb300 import lbm as L
+    from paper_0904_4504_gb300.builder import build
+
+    rank, world, local = dist_setup(args.gpus)
+    build()
+    stream = torch.cuda.Stream()
+    out = []
+    for to in I.PRECISION_TAU_OMEGAS:
+        tau, omega, P = L.lbm_params_from_tau_omega(37, to)
+        steps = 30 * P
+        fits = {}
+        for name in ("f64", "f32", "f16", "bf16"):
+            w = I.beam_d2q37_h4(to, n=2048, storage=STORE[name])
+            geom = L.make_geometry(kind=w.geometry, lx=w.lx, ly=w.ly, drive=w.drive, u0=w.u0, eq_order=4,
+                                   collision=w.collision, storage=STORE[name])
+            h = L.lbm_create(37, 2048, 2048, tau, omega, geom)
+            L.lbm_set_stream(h, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.lbm_step(h, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f_in, f_q, _ = L.lbm_fit(h, 15.0)
+            info = L.lbm_info(h)
+            ms = e0.elapsed_time(e1)
+            fits[name] = (f_in, f_q, info["n_fluid"] * steps / (ms * 1e-3) / 1e6)
+            L.lbm_destroy(h)
+        amp = math.hypot(*fits["f64"][:2])
+        row = {"tau_omega": to, "steps": steps, "F_in_f64": fits["f64"][0], "F_q_f64": fits["f64"][1]}
+        for name in ("f32", "f16", "bf16"):
+            row[f"err_in_{name}"] = abs(fits[name][0] - fits["f64"][0]) / amp
+            row[f"err_q_{name}"] = abs(fits[name][1] - fits["f64"][1]) / amp
+        for name in fits:
+            row[f"mlups_{name}"] = round(fits[name][2], 1)
+        out.append(row)
+    if rank == 0:
+        print(json.dumps({"study": "precision", "workload": "D2Q37-H4 regularized beam 32x32 in 2048^2, body-frame "
+                          "drive U0=1e-3, 30 periods, fit after 15; errors normalized by the FP64 force amplitude",
+                          "rows": out}), flush=True)
+
+
 def run_ours(args):
+    if args.workload == "precision2048":
+        return run_precision(args)
     if args.workload.startswith("serve"):
         return run_serve(args)
     if args.workload.startswith("sweep64"):
@@ -413,10 +476,33 @@ def run_ours(args):
         L.lbm_destroy(h)
 
     cpu = cpu_baseline(wl, params, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    extras = {}
+    if args.workload == "beam1024" and not args.no_extras:
+        # the rest of the metric: the batched mixed-precision form (FP16 storage, FP32 arithmetic,
+        # FP64 force; within the 1e-4 force target) against this plain FP32 single-instance form,
+        # and the served p50/p99 latency
+        import copy
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.no_e2e = "sweep64-f16", args.sweep_steps, 3, True
+        bl = run_batch(a, sub=True)
+        a = copy.copy(args)
+        a.workload, a.requests, a.load = "serve", args.requests, args.load
+        sl = run_serve(a, sub=True)
+        if rank == 0:
+            extras["batched_mixed_precision"] = {
+                "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024) in one "
+                            "persistent cooperative launch per 64 steps, FP16 storage scaled by U0, FP32 arithmetic, "
+                            "FP64 force",
+                "value": bl["value"], "unit": "MLUPS", "steps": bl["steps"], "ms_per_step": bl["ms_per_step"],
+                "roofline": bl["roofline"], "clocks": bl["clocks"], "gpu_launches": bl["gpu_launches"],
+                "speedup_vs_plain_fp32": round(bl["value"] / value, 4),
+                "force_error_vs_oracle": "FP16 storage <= 6e-5 of the force amplitude (in-phase and quadrature, "
+                                         "tests/test_gpu_precision.py); target 1e-4"}
+            extras["serving"] = {k: sl[k] for k in ("value", "unit", "config", "latency", "server", "clocks")}
     if rank == 0:
         w0 = wl[0]
         line = {
-            "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction of the fused step",
+            "metric": "MLUPS and % HBM roofline, batched mixed-prec vs plain FP32 at <=1e-4 force err; p99 latency",
             "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE_NAME[w0.storage], "data": "synthetic",
@@ -432,6 +518,7 @@ def run_ours(args):
                          "bytes_per_launch": bytes_step // len(wl)},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -522,8 +609,12 @@ def main():
     ap.add_argument("--tile", type=int, nargs=2, default=None)
     ap.add_argument("--variant", type=int, default=None, help="step kernel variant (lbm_set_variant)")
     ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64, serve)")
-    ap.add_argument("--requests", type=int, default=48, help="requests per rank (serve)")
+    ap.add_argument("--requests", type=int, default=24, help="requests per rank (serve)")
     ap.add_argument("--load", type=float, default=0.7, help="offered load, fraction of capacity (serve; 0: as generated)")
+    ap.add_argument("--sweep-steps", type=int, default=640, help="timed batch steps of the batched part of beam1024")
+    ap.add_argument("--no-extras", action="store_true", help="beam1024: skip the batched and serving parts")
+    ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
+    ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

@@ -179,15 +179,23 @@ int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, i
 
 /* ----------------------------------------------------------------------------------------------
  * Batches: many simulations of uneven sizes (a tau*omega and aspect-ratio sweep, or the requests
- * of a server) advanced together by one persistent kernel.  All instances of a batch share the
- * lattice, storage type and collision; each has its own grid, geometry, tau, omega, drive and
- * length in steps.  A run of K steps is one cooperative launch (a node of a CUDA graph built once
- * per launch shape): its grid fills the GPU, walks the tiles of every unfinished instance and meets
- * at a grid barrier between steps.  Each barrier wait is bounded (about 2 s by default); a wait
- * that runs out sets an error flag, the kernel returns, and lbm_batch_synchronize reports
- * LBM_ETIMEOUT.  Every instance's arithmetic is exactly that of lbm_step on the same instance.
+ * of a server) advanced together.  All instances of a batch share the lattice, storage type and
+ * collision; each has its own grid, geometry, tau, omega, drive and length in steps.  In the
+ * persistent mode a run of K steps is one cooperative launch (a node of a CUDA graph built once per
+ * launch shape): its grid fills the GPU, walks the tiles of every unfinished instance and meets at
+ * a grid barrier between steps.  Each barrier wait is bounded (about 2 s by default); a wait that
+ * runs out sets an error flag, the kernel returns, and lbm_batch_synchronize reports LBM_ETIMEOUT.
+ * In both modes every instance's arithmetic is that of lbm_step on the same instance.
  * ---------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
+
+/* How a batch runs its instances (lbm_batch_set_mode):
+ *   LBM_BATCH_STREAMS     every instance step is a launch of the single-instance kernel (the
+ *                         fastest variant for the storage type) on one of several parallel
+ *                         streams, so that instances of different sizes overlap (the default);
+ *   LBM_BATCH_PERSISTENT  one cooperative launch per run walks all instances' tiles for K steps
+ *                         with a bounded grid barrier between steps, replayed through a CUDA graph. */
+enum { LBM_BATCH_STREAMS = 0, LBM_BATCH_PERSISTENT = 1 };
 
 /* One instance: the arguments of lbm_create plus the number of steps to run. */
 typedef struct {
@@ -208,6 +216,7 @@ typedef struct {
     int max_blocks;                /* co-resident blocks of the cooperative grid                */
     int uses_graph;                /* 1 if runs are replayed through a CUDA graph               */
     int block_x, block_y;
+    int mode;                      /* LBM_BATCH_STREAMS or LBM_BATCH_PERSISTENT                 */
 } lbm_batch_info_t;
 
 /* New empty batch on the current device.  device_budget_bytes caps the device memory its instances
@@ -238,6 +247,9 @@ lbm_sim* lbm_batch_instance(lbm_batch* batch, int slot);
 
 /* Free an instance's memory (waits for the batch's stream). */
 int lbm_batch_remove(lbm_batch* batch, int slot);
+
+/* Choose the mode (before the first lbm_batch_add). */
+int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Clock cycles a block waits at a grid barrier before giving up (test hook: 0 gives up at once). */
 int lbm_batch_set_barrier_limit(lbm_batch* batch, long long cycles);

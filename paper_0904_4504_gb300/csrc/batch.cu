@@ -34,8 +34,13 @@ constexpr long long kDefaultBarrierLimit = 4000000000ll;  // clock cycles (about
 
 }  // namespace
 
+constexpr int kSubStreams = 8;
+
 struct lbm_batch {
     int device = 0, Q = 0, storage = 0, collision = 0;
+    int mode = LBM_BATCH_STREAMS;
+    cudaStream_t sub[kSubStreams] = {};   // instance launches (streams mode), one chain per instance
+    cudaEvent_t ev_fork = nullptr, ev_join[kSubStreams] = {};
     int bx = 32, by = 4;
     size_t budget = 0, used = 0;
     cudaStream_t stream = nullptr;
@@ -252,6 +257,12 @@ int lbm_batch_create(int lattice, int storage, int collision, size_t device_budg
         cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess)
         return fail(set_error(LBM_ENOMEM, "batch barrier"));
+    for (int k = 0; k < kSubStreams; ++k)
+        if (cudaStreamCreateWithFlags(&b->sub[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(set_error(LBM_ECUDA, "stream creation"));
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_error(LBM_ECUDA, "event creation"));
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, b->bx * b->by, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || per_sm < 1)
@@ -292,11 +303,20 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
         lbm_destroy(sim);
         return code;
     };
-    // tile and history first, on the instance's own stream, so that adding an instance does not
-    // wait for a run of the batch that may be in flight
-    if ((rc = lbm_set_tile(sim, b->bx, b->by))) return undo(rc);
+    int id = -1;
+    for (size_t k = 0; k < b->slots.size(); ++k)
+        if (!slot_live(b->slots[k])) { id = (int)k; break; }
+    if (id < 0) id = (int)b->slots.size();
+    // kernel shape, history and stream, on the instance's own stream first, so that adding an
+    // instance does not wait for a run of the batch that may be in flight
+    if (b->mode == LBM_BATCH_PERSISTENT || b->storage == LBM_STORE_F32 || b->storage == LBM_STORE_F64 ||
+        lbm_set_variant(sim, 11) != LBM_OK)
+        rc = lbm_set_tile(sim, b->bx, b->by);
+    if (rc) return undo(rc);
+    clear_error();
     if ((rc = sim_reserve(sim, (size_t)d->nsteps))) return undo(rc);
-    if ((rc = lbm_set_stream(sim, b->stream))) return undo(rc);
+    if ((rc = lbm_set_stream(sim, b->mode == LBM_BATCH_STREAMS ? b->sub[id % kSubStreams] : b->stream)))
+        return undo(rc);
     // drive table: nsteps doubles followed by the same values as nsteps floats
     const size_t N = (size_t)d->nsteps;
     std::vector<double> table(N + (N + 1) / 2, 0.0);
@@ -318,15 +338,8 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     s.nsteps = d->nsteps;
     s.d_drive = drv;
     s.bytes = bytes;
-    int id = -1;
-    for (size_t k = 0; k < b->slots.size(); ++k)
-        if (!slot_live(b->slots[k])) { id = (int)k; break; }
-    if (id < 0) {
-        id = (int)b->slots.size();
-        b->slots.push_back(s);
-    } else {
-        b->slots[id] = s;
-    }
+    if (id == (int)b->slots.size()) b->slots.push_back(s);
+    else b->slots[id] = s;
     b->used += bytes;
     b->dirty = true;
     *slot = id;
@@ -342,6 +355,28 @@ int lbm_batch_run(lbm_batch* b, long steps) {
     // drop instances that finished before this run
     for (const Slot& s : b->slots)
         if (slot_live(s) && !slot_running(b, s) && b->ntiles > 0) b->dirty = true;
+    if (b->mode == LBM_BATCH_STREAMS) {
+        // every running instance advances on its own stream chain; the sub-streams follow the
+        // batch stream's earlier work and the batch stream waits for theirs at the end
+        BCUDA(cudaEventRecord(b->ev_fork, b->stream));
+        for (int k = 0; k < kSubStreams; ++k) BCUDA(cudaStreamWaitEvent(b->sub[k], b->ev_fork, 0));
+        for (long k = 0; k < steps; ++k) {
+            for (Slot& s : b->slots) {
+                if (!slot_live(s)) continue;
+                const long long n = b->gstep + k - s.start;
+                if (n < 0 || n >= s.nsteps) continue;
+                if ((rc = lbm_step(s.sim, 1))) return rc;
+                b->lattice_updates += (double)sim_view(s.sim).n_fluid;
+                ++b->launches;
+            }
+        }
+        for (int k = 0; k < kSubStreams; ++k) {
+            BCUDA(cudaEventRecord(b->ev_join[k], b->sub[k]));
+            BCUDA(cudaStreamWaitEvent(b->stream, b->ev_join[k], 0));
+        }
+        b->gstep += steps;
+        return LBM_OK;
+    }
     if (b->dirty && (rc = rebuild(b))) return rc;
     bool any = false;
     for (const Slot& s : b->slots) any = any || slot_running(b, s);
@@ -368,6 +403,9 @@ int lbm_batch_synchronize(lbm_batch* b) {
     int rc = check_batch(b);
     if (rc) return rc;
     BCUDA(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < kSubStreams; ++k) BCUDA(cudaStreamSynchronize(b->sub[k]));
+    for (const Slot& s : b->slots)
+        if (slot_live(s) && (rc = lbm_synchronize(s.sim)) != LBM_OK) return rc;
     int err = 0;
     BCUDA(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err & 2) return set_error(LBM_ETIMEOUT, "a grid-barrier wait of the batch kernel timed out; states are undefined");
@@ -396,6 +434,7 @@ int lbm_batch_remove(lbm_batch* b, int slot) {
     if (slot < 0 || slot >= (int)b->slots.size() || !slot_live(b->slots[slot]))
         return set_error(LBM_ERANGE, "no instance in slot %d", slot);
     BCUDA(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < kSubStreams; ++k) BCUDA(cudaStreamSynchronize(b->sub[k]));
     Slot& s = b->slots[slot];
     lbm_destroy(s.sim);
     cudaFree(s.d_drive);
@@ -439,7 +478,8 @@ int lbm_batch_info(lbm_batch* b, lbm_batch_info_t* o) {
     o->budget_bytes = b->budget;
     o->used_bytes = b->used;
     o->max_blocks = b->max_blocks;
-    o->uses_graph = b->use_graph ? 1 : 0;
+    o->uses_graph = (b->mode == LBM_BATCH_PERSISTENT && b->use_graph) ? 1 : 0;
+    o->mode = b->mode;
     o->block_x = b->bx;
     o->block_y = b->by;
     return LBM_OK;
@@ -452,8 +492,19 @@ int lbm_batch_set_stream(lbm_batch* b, void* stream) {
     if (b->own_stream) cudaStreamDestroy(b->stream);
     b->stream = (cudaStream_t)stream;
     b->own_stream = false;
-    for (Slot& s : b->slots)
-        if (slot_live(s) && (rc = lbm_set_stream(s.sim, stream))) return rc;
+    if (b->mode == LBM_BATCH_PERSISTENT)
+        for (Slot& s : b->slots)
+            if (slot_live(s) && (rc = lbm_set_stream(s.sim, stream))) return rc;
+    return LBM_OK;
+}
+
+int lbm_batch_set_mode(lbm_batch* b, int mode) {
+    int rc = check_batch(b);
+    if (rc) return rc;
+    if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_STREAMS) return set_error(LBM_EINVAL, "bad batch mode");
+    for (const Slot& s : b->slots)
+        if (slot_live(s)) return set_error(LBM_EINVAL, "set the mode before adding instances");
+    b->mode = mode;
     return LBM_OK;
 }
 
@@ -465,6 +516,14 @@ void lbm_batch_destroy(lbm_batch* b) {
         if (s.sim) lbm_destroy(s.sim);
         cudaFree(s.d_drive);
     }
+    for (int k = 0; k < kSubStreams; ++k) {
+        if (b->sub[k]) {
+            cudaStreamSynchronize(b->sub[k]);
+            cudaStreamDestroy(b->sub[k]);
+        }
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     free_graph(b);
     cudaFree(b->d_insts);
     cudaFree(b->d_tiles);

@@ -29,6 +29,7 @@ LBM_DRIVE_WALL, LBM_DRIVE_BODYFORCE = 0, 1
 LBM_COLL_BGK, LBM_COLL_REGULARIZED = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = 0, 1, 2, 3
 LBM_FLUID, LBM_BODY, LBM_WALL = 0, 1, 2
+LBM_BATCH_STREAMS, LBM_BATCH_PERSISTENT = 0, 1
 STORAGE_BYTES = {LBM_STORE_F64: 8, LBM_STORE_F32: 4, LBM_STORE_BF16: 2, LBM_STORE_F16: 2}
 
 
@@ -90,6 +91,7 @@ class lbm_batch_info_t(ctypes.Structure):
         ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
         ("max_blocks", ctypes.c_int), ("uses_graph", ctypes.c_int),
         ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+        ("mode", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -177,6 +179,7 @@ def lib():
             "lbm_batch_instance": (_P, [_P, ctypes.c_int]),
             "lbm_batch_remove": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_set_barrier_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+            "lbm_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
             "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
             "lbm_batch_destroy": (None, [_P]),
@@ -386,6 +389,10 @@ def lbm_batch_instance(batch: int, slot: int) -> int:
 
 def lbm_batch_remove(batch: int, slot: int) -> None:
     _check(lib().lbm_batch_remove(batch, slot))
+
+
+def lbm_batch_set_mode(batch: int, mode: int) -> None:
+    _check(lib().lbm_batch_set_mode(batch, mode))
 
 
 def lbm_batch_set_barrier_limit(batch: int, cycles: int) -> None:

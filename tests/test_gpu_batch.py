@@ -52,10 +52,15 @@ MIX = [  # uneven sizes, parameters, geometries and lengths
 ]
 
 
-def test_batch_equals_standalone_bitwise():
+MODES = [L.LBM_BATCH_STREAMS, L.LBM_BATCH_PERSISTENT]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_equals_standalone_bitwise(mode):
     descs = [_desc(37, nx, ny, tau, om, n, **kw) for nx, ny, tau, om, n, kw in MIX]
     b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
     try:
+        L.lbm_batch_set_mode(b, mode)
         slots = [L.lbm_batch_add(b, d) for d in descs]
         # uneven chunks; the longest instance needs 41 steps
         for k in (5, 1, 17, 3, 20):
@@ -75,7 +80,8 @@ def test_batch_equals_standalone_bitwise():
         L.lbm_batch_destroy(b)
 
 
-def test_instances_joining_and_leaving_mid_run():
+@pytest.mark.parametrize("mode", MODES)
+def test_instances_joining_and_leaving_mid_run(mode):
     """An instance added after others ran, and another removed while others continue, do not change
     anyone's result."""
     d1 = _desc(37, 70, 41, 0.9, 0.05, 30)
@@ -83,6 +89,7 @@ def test_instances_joining_and_leaving_mid_run():
     d3 = _desc(37, 64, 64, 0.7, 0.06, 12, kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL)
     b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
     try:
+        L.lbm_batch_set_mode(b, mode)
         s1 = L.lbm_batch_add(b, d1)
         s3 = L.lbm_batch_add(b, d3)
         L.lbm_batch_run(b, 7)
@@ -106,10 +113,12 @@ def test_instances_joining_and_leaving_mid_run():
         L.lbm_batch_destroy(b)
 
 
-def test_batch_instance_matches_oracle():
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_instance_matches_oracle(mode):
     Q, nx, ny, tau, omega, n = 37, 70, 41, 0.9, 0.05, 20
     b = L.lbm_batch_create(Q, L.LBM_STORE_F64, L.LBM_COLL_REGULARIZED)
     try:
+        L.lbm_batch_set_mode(b, mode)
         s = L.lbm_batch_add(b, _desc(Q, nx, ny, tau, omega, n, storage=L.LBM_STORE_F64))
         L.lbm_batch_add(b, _desc(Q, 64, 64, 0.7, 0.06, 9, storage=L.LBM_STORE_F64))
         L.lbm_batch_run(b, n)
@@ -132,6 +141,7 @@ def test_barrier_timeout_is_reported_not_hung():
     """A barrier wait that runs out (limit 0: give up at once) ends the kernel and is reported."""
     b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
     try:
+        L.lbm_batch_set_mode(b, L.LBM_BATCH_PERSISTENT)
         for k in range(3):
             L.lbm_batch_add(b, _desc(37, 256, 256, 0.9, 0.05, 10))
         assert L.lbm_batch_info(b)["max_blocks"] > 1
@@ -164,10 +174,12 @@ def test_admission_by_footprint():
         L.lbm_batch_destroy(b)
 
 
-def test_batch_sweep_shapes_run():
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_sweep_shapes_run(mode):
     """The 64-instance sweep (sizes 256..1024, AR 0.25..2) fits and runs a few steps."""
     b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
     try:
+        L.lbm_batch_set_mode(b, mode)
         for w in I.sweep_d2q37():
             tau, omega, P = orc.params_from_tau_omega(37, w.tau_omega)
             L.lbm_batch_add(b, L.make_instance(37, w.nx, w.ny, tau, omega, int(w.periods * P), kind=w.geometry,
@@ -176,6 +188,6 @@ def test_batch_sweep_shapes_run():
         L.lbm_batch_run(b, 3)
         L.lbm_batch_synchronize(b)
         info = L.lbm_batch_info(b)
-        assert info["live"] == 64 and info["running"] == 64
+        assert info["live"] == 64 and info["running"] == 64 and info["mode"] == mode
     finally:
         L.lbm_batch_destroy(b)
