@@ -126,7 +126,12 @@ int lbm_set_stream(lbm_sim* sim, void* stream);
 int lbm_get_state(lbm_sim* sim, double* out, size_t count);
 
 /* Overwrite the current state with deviations g (same layout as lbm_get_state), rounded to the
- * storage type.  Values at solid nodes are ignored (solid nodes hold g = 0). */
+ * storage type.  Values at solid nodes are ignored (solid nodes hold g = 0).
+ * Storage convention: the device holds h_i = (f_i - w_i rho0) / (w_i s), s = u0 for 16-bit storage
+ * and 1 otherwise; 16-bit runs with the body-force drive store h_i - H_i(n) instead, H_i(n) being
+ * h_i of the equilibrium at rho0 of the uniform stream U(n) = sum_{k<n} u0 omega cos(omega (k+1/2))
+ * (the flow the body force sets up far from the body), so that the stored values, and their
+ * rounding errors, are small away from the body.  lbm_get_state and lbm_set_state convert. */
 int lbm_set_state(lbm_sim* sim, const double* g, size_t count);
 
 /* Node labels (ny*nx, row-major) the simulation runs with. */

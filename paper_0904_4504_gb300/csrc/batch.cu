@@ -309,6 +309,7 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     if (id < 0) id = (int)b->slots.size();
     // kernel shape, history and stream, on the instance's own stream first, so that adding an
     // instance does not wait for a run of the batch that may be in flight
+    if (b->mode == LBM_BATCH_PERSISTENT) sim_disable_stream_offset(sim);  // the kernel reads fixed params
     if (b->mode == LBM_BATCH_PERSISTENT || b->storage == LBM_STORE_F32 || b->storage == LBM_STORE_F64 ||
         lbm_set_variant(sim, 11) != LBM_OK)
         rc = lbm_set_tile(sim, b->bx, b->by);

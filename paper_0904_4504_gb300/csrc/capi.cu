@@ -364,7 +364,9 @@ struct lbm_sim {
     bool own_stream = false;
     int bx = 32, by = 4, ntx = 0, ntiles = 0, nslots = 0;
     int plain_bx = 32, plain_by = 4;   // tile of the plain kernel (lbm_set_tile)
-    int variant = 0;                   // 0 plain kernel; 2, 3: TMA kernel with that many stages
+    int variant = 0;                   // 0 plain kernel, else a staged variant (lbm_set_variant)
+    bool stream_off = false;           // 16-bit body frame: store h - H(U(n)), see InstDev
+    double U_stream = 0.0;             // U(n) = sum_{k<n} g(k + 1/2) for n = steps_done
     StepLaunchFn launch = nullptr;
     TmaStepLaunchFn tma_launch = nullptr;
     CUtensorMap maps[2];
@@ -447,6 +449,29 @@ int ensure_capacity(lbm_sim* s, size_t need) {
     return LBM_OK;
 }
 
+// Scaled equilibrium deviation H_i of the uniform stream U x (no rest term), and its moments.
+void stream_offset(const lbm_sim* s, double U, float* H, float* HM) {
+    const HostLattice& L = s->lat;
+    const double b = U * U / L.theta;
+    double M[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < L.Q; ++i) {
+        const double a = L.c[i][0] * U / L.theta;
+        double poly = a + 0.5 * (a * a - b);
+        if (s->geom.eq_order >= 4) poly += (a * a * a - 3 * a * b) / 6.0 + (a * a * a * a - 6 * a * a * b + 3 * b * b) / 24.0;
+        const double Hi = s->geom.rho0 * poly / s->dev.s;
+        H[i] = (float)Hi;
+        const double w = L.w[i], cx = L.c[i][0], cy = L.c[i][1];
+        M[0] += w * H[i];
+        M[1] += w * cx * H[i];
+        M[2] += w * cy * H[i];
+        M[3] += w * cx * cx * H[i];
+        M[4] += w * cx * cy * H[i];
+        M[5] += w * cy * cy * H[i];
+    }
+    if (HM)
+        for (int k = 0; k < 6; ++k) HM[k] = (float)M[k];
+}
+
 int check_sim(lbm_sim* s) {
     if (!s) return set_error(LBM_EINVAL, "null simulation");
     CUDA_TRY(cudaSetDevice(s->device));
@@ -485,6 +510,11 @@ SimView sim_view(const lbm_sim* s) {
 }
 
 int sim_reserve(lbm_sim* s, size_t steps) { return ensure_capacity(s, steps); }
+
+void sim_disable_stream_offset(lbm_sim* s) {
+    if (s->steps_done == 0) s->stream_off = false;
+    s->dev.stream_off = s->stream_off ? 1 : 0;
+}
 
 void sim_advance(lbm_sim* s, long steps) {
     s->steps_done += steps;
@@ -650,6 +680,7 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.omega_c_f = (float)d.omega_c;
     d.reg_a_f = (float)d.reg_a;
     d.src_k_f = (float)d.src_k;
+    s->stream_off = es == 2 && g.drive == LBM_DRIVE_BODYFORCE;
     TRY_OR_FREE(setup_tiles(s));
     TRY_OR_FREE(ensure_capacity(s, 1024));
     *out = s;
@@ -703,12 +734,18 @@ int lbm_step(lbm_sim* s, long n) {
         s->dev.dst = s->buf[s->cur ^ 1];
         s->dev.dv = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done);
         s->dev.dv_f = (float)s->dev.dv;
+        s->dev.stream_off = s->stream_off ? 1 : 0;
+        if (s->stream_off) {
+            stream_offset(s, s->U_stream, s->dev.Hl, s->dev.HM);
+            stream_offset(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+        }
         s->dev.force_out = s->d_history + s->steps_done;
         const cudaError_t e = s->tma_launch ? s->tma_launch(s->dev, s->maps[s->cur], s->stream)
                                             : s->launch(s->dev, block, s->stream);
         if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
         ++s->steps_done;
+        if (s->stream_off) s->U_stream += s->dev.dv;
     }
     return LBM_OK;
 }
@@ -807,12 +844,18 @@ int lbm_get_state(lbm_sim* s, double* out, size_t count) {
     if (!out || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
     std::vector<unsigned char> host(plane * s->Q * s->esize);
     CUDA_TRY(cudaMemcpy(host.data(), s->buf[s->cur], host.size(), cudaMemcpyDeviceToHost));
+    float H[37] = {0};
+    if (s->stream_off) stream_offset(s, s->U_stream, H, nullptr);
     for (int i = 0; i < s->Q; ++i) {
         const double scale = s->lat.w[i] * s->dev.s;
         for (int y = 0; y < s->ny; ++y)
-            for (int x = 0; x < s->nx; ++x)
-                out[(size_t)i * N + (size_t)y * s->nx + x] =
-                    scale * to_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x);
+            for (int x = 0; x < s->nx; ++x) {
+                const size_t k = (size_t)y * s->nx + x;
+                const double v = to_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x);
+                // with the stream offset the kernel forms h = stored + H in FP32; do the same here
+                const double h = s->stream_off ? (double)(float)(v + H[i]) : v;
+                out[(size_t)i * N + k] = s->labels[k] ? 0.0 : scale * h;
+            }
     }
     return rc;
 }
@@ -823,12 +866,14 @@ int lbm_set_state(lbm_sim* s, const double* g, size_t count) {
     const size_t N = (size_t)s->nx * s->ny, plane = (size_t)s->ny * s->pitch;
     if (!g || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
     std::vector<unsigned char> host(plane * s->Q * s->esize, 0);
+    float H[37] = {0};
+    if (s->stream_off) stream_offset(s, s->U_stream, H, nullptr);
     for (int i = 0; i < s->Q; ++i) {
         const double inv = 1.0 / (s->lat.w[i] * s->dev.s);
         for (int y = 0; y < s->ny; ++y)
             for (int x = 0; x < s->nx; ++x) {
                 const size_t k = (size_t)y * s->nx + x;
-                const double v = s->labels[k] ? 0.0 : g[(size_t)i * N + k] * inv;
+                const double v = s->labels[k] ? 0.0 : g[(size_t)i * N + k] * inv - (double)H[i];
                 from_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x, v);
             }
     }

@@ -48,6 +48,8 @@ struct SimView {
 SimView sim_view(const lbm_sim* s);
 // Make room for `steps` entries of force history (may allocate).
 int sim_reserve(lbm_sim* s, size_t steps);
+// Store plain scaled deviations (no uniform-stream offset); only before the first step.
+void sim_disable_stream_offset(lbm_sim* s);
 // Record that `steps` steps were run on the simulation's buffers by another launcher.
 void sim_advance(lbm_sim* s, long steps);
 

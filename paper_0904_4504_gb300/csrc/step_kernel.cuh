@@ -63,6 +63,14 @@ struct InstDev {
     // FP32 copies of the constants above (and of dv), so that FP32 arithmetic converts nothing per
     // node: double -> float conversions run on the FP64 pipe, which is slow on this GPU
     float dv_f, rho0_f, s_f, inv_s_f, omega_c_f, reg_a_f, src_k_f, pad_f;
+    // 16-bit body-frame runs store h_i - H_i(n), with H_i(n) the (scaled) equilibrium deviation of
+    // the uniform stream U(n) = sum_{k<n} g(k + 1/2) that the body force sets up; far from the body
+    // the stored values are then small and so are their rounding errors.  Hl: H of the state read,
+    // Hs: H of the state written, HM: moments sum_i w_i {1, c, cc} H_i of Hl (scaled units).
+    int stream_off;
+    float HM[6];
+    float Hl[37];
+    float Hs[37];
 };
 
 // A launch constant in the arithmetic type T: the double itself, or its FP32 copy.
@@ -181,6 +189,13 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
     const long long plane = P.plane;
     const int idx = y * P.pitch + x;
 
+    // stored values relative to the uniform stream: plain BGK needs every h_i, the regularized
+    // collision only their moments (HM is added to those below)
+    const bool off = SCALED && P.stream_off;
+    if (off && COLL == COLL_BGK) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) h[i] += (T)P.Hl[i];
+    }
     // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
     // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
     if (cls == NODE_BOUNDARY) {
@@ -190,7 +205,8 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
         for (int i = 1; i < Q; ++i) {
             if ((blk >> i) & 1ull) {
                 const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-                const T own = S::ld(src + opp_of<L>(i) * plane + idx);
+                T own = S::ld(src + opp_of<L>(i) * plane + idx);
+                if (off) own += (T)P.Hl[opp_of<L>(i)];
                 double mw = 0.0;
                 if ((lk.x >> i) & 1ull) {
                     if (P.moving) mw = P.mw_k * cx * dv;
@@ -201,6 +217,8 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
                     Fy -= cy * ws * hs;
                 }
                 h[i] = own + (T)mw;
+                // the regularized path keeps h relative to the stream until the moments
+                if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
             }
         }
     }
@@ -221,6 +239,10 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
         if (py) pyy += (T)(w * py * py) * sp;
     }
     if (SCALED) {
+        if (off && COLL == COLL_REG) {
+            m0 += (T)P.HM[0]; jx += (T)P.HM[1]; jy += (T)P.HM[2];
+            pxx += (T)P.HM[3]; pxy += (T)P.HM[4]; pyy += (T)P.HM[5];
+        }
         const T s = kconst<T>(P.s, P.s_f);
         m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
     }
@@ -328,11 +350,16 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     const int idx = y * P.pitch + x;
     Coef<T> C;
     prepare<L, ST, COLL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
-    S::st(dst + idx, eval_rest<L, COLL, T>(C, h[0]));
+    const bool off = sizeof(ST) == 2 && P.stream_off;
+    S::st(dst + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)P.Hs[0] : (T)0));
 #pragma unroll
     for (int k = 0; k < L::NP; ++k) {
         T op, omn;
         eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
+        if (off) {
+            op -= (T)P.Hs[1 + 2 * k];
+            omn -= (T)P.Hs[2 + 2 * k];
+        }
         S::st(dst + (1 + 2 * k) * plane + idx, op);
         S::st(dst + (2 + 2 * k) * plane + idx, omn);
     }

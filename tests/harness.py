@@ -47,3 +47,17 @@ def scaled(Q: int, g: np.ndarray) -> np.ndarray:
     """h = g / w: every direction on the same footing."""
     _, w, _ = L.lbm_lattice_velocities(Q)
     return g / w[:, None, None]
+
+
+def stream_offset_magnitude(Q: int, u0: float, omega: float, n: int, eq_order: int, rho0: float = 1.0) -> np.ndarray:
+    """|H_i| of the 16-bit body-frame storage convention (include/lbm.h): the scaled equilibrium
+    deviation of the uniform stream U(n) = sum_{k<n} u0 omega cos(omega (k + 1/2)); 16-bit storage
+    rounds h - H, so its rounding error is bounded relative to |h| + |H|.  Tolerances only."""
+    c, w, th = L.lbm_lattice_velocities(Q)
+    U = sum(u0 * omega * np.cos(omega * (k + 0.5)) for k in range(n))
+    a = c[:, 0] * U / th
+    b = U * U / th
+    poly = a + 0.5 * (a * a - b)
+    if eq_order >= 4:
+        poly = poly + (a ** 3 - 3 * a * b) / 6.0 + (a ** 4 - 6 * a * a * b + 3 * b * b) / 24.0
+    return np.abs(rho0 * poly / u0)
