@@ -45,6 +45,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current step kernels,
+# from one ncu capture each (profiles/*.md); a kernel change invalidates its entry.
+TRAFFIC = {("beam1024", 0): 156.369664e6 + 109.401344e6,      # step_kernel<D2Q37, float, 1>
+           ("beam1024x1", 0): 156.369664e6 + 109.401344e6,
+           ("beam1024x1-f16", 11): 78.781696e6 + 38.216704e6}  # step_kernel_tma1<D2Q37, half, 1, 64, 2>
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 
@@ -513,7 +519,9 @@ def run_ours(args):
                              "inputs smaller than L2", "parallelism": f"replicas x{world}",
                        "tile": [infos[0]["block_x"], infos[0]["block_y"]], "variant": infos[0]["variant"]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                         "frac": round(achieved / peak, 4),
+                         "traffic": args.traffic if args.traffic is not None else
+                         TRAFFIC.get((args.workload, infos[0]["variant"])),
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": "step_kernel (fused stream+collide+force)",
                          "bytes_per_launch": bytes_step // len(wl)},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
