@@ -169,6 +169,22 @@ int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
  * LBM_EINVAL if the variant is not built for the simulation's storage type. */
 int lbm_set_variant(lbm_sim* sim, int variant);
 
+/* One candidate of the autotuner: kernel variant (0 = plain kernel with tile block_x x block_y) and
+ * its measured time per step. */
+typedef struct {
+    int variant, block_x, block_y;
+    double us_per_step;
+} lbm_tune_entry;
+
+/* Time every step-kernel candidate built for the simulation's lattice/storage/collision (plain
+ * kernel tiles and staged variants) for `steps` steps each, on a clone of the simulation (same
+ * geometry, parameters and storage; the simulation itself is not advanced).  Fills up to cap
+ * entries of out and sets *n to the number timed.  Needs device memory for the clone. */
+int lbm_tune(lbm_sim* sim, int steps, lbm_tune_entry* out, int cap, int* n);
+
+/* lbm_tune, then switch the simulation to the fastest candidate (reported in *best if not NULL). */
+int lbm_autotune(lbm_sim* sim, int steps, lbm_tune_entry* best);
+
 /* Velocity table of a lattice in the library's direction order: c_xy[2i], c_xy[2i+1], w[i], theta.
  * Any output may be NULL.  Returns Q, or LBM_EINVAL. */
 int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta);

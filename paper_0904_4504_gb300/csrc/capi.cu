@@ -889,6 +889,66 @@ int lbm_get_labels(lbm_sim* s, unsigned char* out, size_t count) {
     return LBM_OK;
 }
 
+int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
+    int rc = check_sim(s);
+    if (rc) return rc;
+    if (steps < 1 || !n_out || (cap > 0 && !out)) return set_error(LBM_EINVAL, "need steps >= 1 and an output");
+    // candidates: plain kernel tiles, then every staged variant built for this storage type
+    const int tiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {32, 2}};
+    const int variants[] = {10, 11, 12, 20, 21, 22};
+    std::vector<lbm_tune_entry> cand;
+    for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
+    for (int v : variants)
+        if (find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, v)) {
+            int bx = 0, by = 0;
+            variant_tile(v, &bx, &by);
+            cand.push_back(lbm_tune_entry{v, bx, by, 0.0});
+        }
+    // a clone with the same geometry (as a label mask), parameters and storage
+    lbm_geometry g = s->geom;
+    g.kind = LBM_GEOM_MASK;
+    g.mask = s->labels.data();
+    lbm_sim* c = nullptr;
+    if ((rc = lbm_create(s->Q, s->nx, s->ny, s->tau, s->omega, &g, &c))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int k = 0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = set_error(LBM_ECUDA, "events");
+    for (auto& e : cand) {
+        if (rc) break;
+        rc = e.variant ? lbm_set_variant(c, e.variant) : lbm_set_tile(c, e.block_x, e.block_y);
+        if (rc) break;
+        if ((rc = lbm_step(c, 2))) break;  // warm-up (first launch sets kernel attributes)
+        cudaEventRecord(e0, c->stream);
+        if ((rc = lbm_step(c, steps))) break;
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_error(LBM_ECUDA, "event sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        e.us_per_step = 1000.0 * ms / steps;
+        if (k < cap) out[k] = e;
+        ++k;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    lbm_destroy(c);
+    *n_out = k;
+    return rc;
+}
+
+int lbm_autotune(lbm_sim* s, int steps, lbm_tune_entry* best) {
+    lbm_tune_entry e[32];
+    int n = 0;
+    int rc = lbm_tune(s, steps, e, 32, &n);
+    if (rc) return rc;
+    if (n == 0) return set_error(LBM_EINVAL, "no candidate");
+    int b = 0;
+    for (int k = 1; k < n; ++k)
+        if (e[k].us_per_step < e[b].us_per_step) b = k;
+    rc = e[b].variant ? lbm_set_variant(s, e[b].variant) : lbm_set_tile(s, e[b].block_x, e[b].block_y);
+    if (rc == LBM_OK && best) *best = e[b];
+    return rc;
+}
+
 int lbm_info(lbm_sim* s, lbm_info_t* o) {
     int rc = check_sim(s);
     if (rc) return rc;

@@ -98,6 +98,11 @@ class lbm_batch_info_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class lbm_tune_entry(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("us_per_step", ctypes.c_double)]
+
+
 class lbm_request(ctypes.Structure):
     _fields_ = [("desc", lbm_instance_desc), ("skip_periods", ctypes.c_double), ("perimeter", ctypes.c_double)]
 
@@ -164,6 +169,9 @@ def lib():
             "lbm_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_info_t)]),
             "lbm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
             "lbm_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_tune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lbm_tune_entry), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int)]),
+            "lbm_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(lbm_tune_entry)]),
             "lbm_lattice_velocities": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D]),
             "lbm_params_from_tau_omega": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                          _D, _D, ctypes.POINTER(ctypes.c_int)]),
@@ -328,6 +336,20 @@ def lbm_set_tile(sim: int, block_x: int, block_y: int) -> None:
 
 def lbm_set_variant(sim: int, variant: int) -> None:
     _check(lib().lbm_set_variant(sim, variant))
+
+
+def lbm_tune(sim: int, steps: int = 20) -> list[dict]:
+    """Time every kernel candidate on a clone; list of {variant, block_x, block_y, us_per_step}."""
+    out = (lbm_tune_entry * 32)()
+    n = ctypes.c_int()
+    _check(lib().lbm_tune(sim, steps, out, 32, ctypes.byref(n)))
+    return [{f: getattr(out[k], f) for f, _ in lbm_tune_entry._fields_} for k in range(n.value)]
+
+
+def lbm_autotune(sim: int, steps: int = 20) -> dict:
+    best = lbm_tune_entry()
+    _check(lib().lbm_autotune(sim, steps, ctypes.byref(best)))
+    return {f: getattr(best, f) for f, _ in lbm_tune_entry._fields_}
 
 
 def lbm_step_noalloc(sim: int, n: int, g_in: int, g_out: int, force_out: int, stream=None) -> None:
