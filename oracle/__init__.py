@@ -35,6 +35,8 @@ DRIVE_WALL = 0   # label-1 solid moves with U_w = u0 sin(omega t) x
 DRIVE_BODY = 1   # body frame: fluid force density rho * u0 omega cos(omega t) x, walls static
 COLL_BGK = 0
 COLL_REG = 1
+WALL_BB = 0      # bounce-back, Eq. 12
+WALL_DS = 1      # diffuse scattering, Eq. 11
 
 
 class _Params(ctypes.Structure):
@@ -50,6 +52,7 @@ class _Params(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("drive", ctypes.c_int),
         ("label", ctypes.POINTER(ctypes.c_ubyte)),
+        ("wall", ctypes.c_int),
     ]
 
 
@@ -153,7 +156,7 @@ def rest_state(Q: int, nx: int, ny: int, rho0: float = 1.0) -> np.ndarray:
 
 
 def run(Q, label, tau, omega, u0, nsteps, *, rho0=1.0, eq_order=2, collision=COLL_REG, drive=DRIVE_WALL,
-        f=None, n0=0, nthreads=1):
+        f=None, n0=0, nthreads=1, wall=WALL_BB):
     """Advance the post-collision state f ([ny][nx][Q], full populations) by nsteps steps starting
     at step n0; returns (f, force) with force[k] = (Fx, Fy) on the label-1 body during step n0+k."""
     label = np.ascontiguousarray(label, dtype=np.uint8)
@@ -164,7 +167,7 @@ def run(Q, label, tau, omega, u0, nsteps, *, rho0=1.0, eq_order=2, collision=COL
     assert f.shape == (ny, nx, Q)
     force = np.zeros((max(nsteps, 0), 2))
     p = _Params(Q, nx, ny, tau, omega, u0, rho0, eq_order, collision, drive,
-                label.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+                label.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), wall)
     rc = _load().oracle_run(ctypes.byref(p), n0, nsteps, _dptr(f), _dptr(force), nthreads)
     if rc:
         raise ValueError(f"oracle_run failed ({rc})")

@@ -27,7 +27,11 @@
  *   - body force: Guo-type source with half-force velocity; in the regularized collision the
  *     projected non-equilibrium part keeps its first Hermite moment (zero without a force, -F/2
  *     with one), so that total momentum grows by exactly F per step;
- *   - force on the body: momentum exchange summed over every link blocked by a body node.
+ *   - force on the body: momentum exchange summed over every link blocked by a body node;
+ *   - diffuse scattering (Eq. 11) on the lattice: at a fluid node, the populations coming back from
+ *     a wall along its blocked links are the wall's discrete Maxwellian (the equilibrium of the
+ *     run's order at the wall velocity) with the density that returns exactly the mass the node
+ *     sends into that wall (zero net normal mass flux), per wall.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -180,6 +184,7 @@ typedef struct {
     int drive;                   /* 0: label-1 wall moves with U_w = u0 sin(wt) x; 1: body force
                                     g = u0 w cos(wt) x on the fluid, all walls static            */
     const unsigned char* label;  /* ny*nx row-major: 0 fluid, 1 body (force counted), 2 wall    */
+    int wall;                    /* 0: bounce-back (Eq. 12); 1: diffuse scattering (Eq. 11)      */
 } oracle_params;
 
 static int gcd_int(int a, int b) {
@@ -196,7 +201,8 @@ static void node_update(const olat* L, const oracle_params* p, const double* f, 
     const double* fx = f + ((size_t)y * p->nx + x) * Q;
     double th = L->theta, rho = 0, jx = 0, jy = 0, ux, uy, Fbx, Fby;
 
-    /* Eq. 17 with Eq. 12 on blocked links */
+    /* Eq. 17; links blocked by a solid get Eq. 12 or Eq. 11 below */
+    int blocked[OQMAX];
     for (i = 0; i < Q; ++i) {
         int cx = L->c[i][0], cy = L->c[i][1];
         int g = gcd_int(abs(cx), abs(cy)), hit = 0, sx = x, sy = y;
@@ -207,18 +213,36 @@ static void node_update(const olat* L, const oracle_params* p, const double* f, 
             sy = ((y - k * cy / g) % p->ny + p->ny) % p->ny;
             if (p->label[(size_t)sy * p->nx + sx]) { hit = p->label[(size_t)sy * p->nx + sx]; break; }
         }
-        if (!hit) {
-            fadv[i] = f[((size_t)sy * p->nx + sx) * Q + i];
-        } else {
-            double u_wall = (hit == 1 && p->drive == 0) ? uw : 0.0;
-            fadv[i] = fx[L->opp[i]] + 2.0 * L->w[i] * p->rho0 * (cx * u_wall) / th;
-            if (hit == 1) {
-                /* momentum carried in by f_opp (velocity -c_i) and out by f_i^adv (velocity c_i) */
-                *Fx += -cx * (fx[L->opp[i]] + fadv[i]);
-                *Fy += -cy * (fx[L->opp[i]] + fadv[i]);
-            }
+        blocked[i] = hit;
+        if (!hit) fadv[i] = f[((size_t)sy * p->nx + sx) * Q + i];
+    }
+    if (p->wall == 0) {
+        /* Eq. 12: the node's own opposite population comes back, plus 2 w_i rho0 c_i.U_w / theta */
+        for (i = 0; i < Q; ++i) {
+            if (!blocked[i]) continue;
+            double u_wall = (blocked[i] == 1 && p->drive == 0) ? uw : 0.0;
+            fadv[i] = fx[L->opp[i]] + 2.0 * L->w[i] * p->rho0 * (L->c[i][0] * u_wall) / th;
+        }
+    } else {
+        /* Eq. 11: wall Maxwellian at U_w, density from zero net mass flux into each wall */
+        int lab;
+        for (lab = 1; lab <= 2; ++lab) {
+            double u_wall = (lab == 1 && p->drive == 0) ? uw : 0.0, feq1[OQMAX], in = 0.0, den = 0.0, rho_w;
+            equilibrium(L, p->eq_order, 1.0, u_wall, 0.0, feq1);
+            for (i = 0; i < Q; ++i)
+                if (blocked[i] == lab) { in += fx[L->opp[i]]; den += feq1[i]; }
+            if (den == 0.0) continue;
+            rho_w = in / den;
+            for (i = 0; i < Q; ++i)
+                if (blocked[i] == lab) fadv[i] = rho_w * feq1[i];
         }
     }
+    /* momentum carried into the body by f_opp (velocity -c_i) and out by f_i^adv (velocity c_i) */
+    for (i = 0; i < Q; ++i)
+        if (blocked[i] == 1) {
+            *Fx += -L->c[i][0] * (fx[L->opp[i]] + fadv[i]);
+            *Fy += -L->c[i][1] * (fx[L->opp[i]] + fadv[i]);
+        }
     /* Eq. 16 */
     for (i = 0; i < Q; ++i) {
         rho += fadv[i];
@@ -259,6 +283,7 @@ int oracle_run(const oracle_params* p, long n0, long nsteps, double* f, double* 
     if (p->nx < 1 || p->ny < 1 || !(p->tau > 0.5) || (p->eq_order != 2 && p->eq_order != 4)) return -1;
     if (p->collision != 0 && p->collision != 1) return -1;
     if (p->drive != 0 && p->drive != 1) return -1;
+    if (p->wall != 0 && p->wall != 1) return -1;
     N = (size_t)p->nx * p->ny * L.Q;
     tmp = (double*)malloc(N * sizeof(double));
     rowF = (double*)malloc((size_t)p->ny * 2 * sizeof(double));

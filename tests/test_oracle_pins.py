@@ -330,3 +330,72 @@ def test_params_from_tau_omega():
         assert P == 128 and abs((tl - 0.5) * om - to) < 1e-12 * to
     tl, om, P = orc.params_from_tau_omega(9, 1e-3)
     assert P == math.ceil(8 * math.pi / math.sqrt(2 / 3 * 1e-3))
+
+
+# ------------------------------------------------------------------------------------------------
+# diffuse-scattering walls (Eq. 11)
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q,order,coll", CASES)
+def test_diffuse_walls_conserve_mass_and_balance_momentum(Q, order, coll):
+    nx, ny = 26, 22
+    lab = orc.geometry_beam(nx, ny, 7, 6)
+    lab[0, :] = 2                                     # a static wall row as well
+    if Q == 37:
+        lab[:3, :] = 2
+    f = _perturbed(Q, nx, ny, lab, 4)
+    tau, omega, u0, n0 = 0.85, 0.21, 2e-3, 3
+    prev = _mass_momentum(Q, f, lab)
+    M = prev[0]
+    f1, F = orc.run(Q, lab, tau, omega, u0, 1, eq_order=order, collision=coll, drive=orc.DRIVE_BODY, f=f, n0=n0,
+                    wall=orc.WALL_DS)
+    cur = _mass_momentum(Q, f1, lab)
+    assert abs(cur[0] - M) < 1e-13 * M
+    # the static wall row takes momentum too: only a body-only box gives the exact balance below
+    lab2 = orc.geometry_beam(nx, ny, 7, 6)
+    f = _perturbed(Q, nx, ny, lab2, 5)
+    prev = _mass_momentum(Q, f, lab2)
+    f1, F = orc.run(Q, lab2, tau, omega, u0, 1, eq_order=order, collision=coll, drive=orc.DRIVE_BODY, f=f, n0=n0,
+                    wall=orc.WALL_DS)
+    cur = _mass_momentum(Q, f1, lab2)
+    g = u0 * omega * math.cos(omega * (n0 + 0.5))
+    assert abs((cur[1] - prev[1]) - (prev[0] * g - F[0, 0])) < 2e-14 * prev[0]
+    assert abs((cur[2] - prev[2]) - (0.0 - F[0, 1])) < 2e-14 * prev[0]
+
+
+@pytest.mark.parametrize("Q", [37, 9])
+def test_free_molecular_diffuse_plate_is_half_bounce_back(Q):
+    """Sec. 4.1: F^BB = 2 F^DS in free-molecular flow.  Collisionless gas at rest on a tangential
+    plate: the diffuse wall returns w_i rho_w (1 + c_i.U/theta + O(U^2)) with rho_w = rho0 (1 + O(U^2)),
+    so F_x = -(rho0 U / theta) S_nt per unit length, half the bounce-back value."""
+    S_nt, _, th = _lattice_sums(Q)
+    nx, ny, omega, u0 = 5, 60, 0.05, 1e-3
+    lab = orc.geometry_plate(Q, nx, ny)
+    _, F_ds = orc.run(Q, lab, 1e15, omega, u0, 8, collision=orc.COLL_BGK, drive=orc.DRIVE_WALL, wall=orc.WALL_DS)
+    _, F_bb = orc.run(Q, lab, 1e15, omega, u0, 8, collision=orc.COLL_BGK, drive=orc.DRIVE_WALL, wall=orc.WALL_BB)
+    for n in range(8):
+        U = u0 * math.sin(omega * (n + 0.5))
+        expect = -U / th * S_nt * nx
+        # O(U^2) from rho_w, and FP64 sums of link terms of size w rho0
+        assert abs(F_ds[n, 0] - expect) < 1e-6 * abs(expect) + 1e-12 * u0 * nx
+        assert abs(F_bb[n, 0] - 2.0 * expect) < 1e-12 * u0 * nx
+
+
+def test_diffuse_slip_reduction_goes_from_continuum_to_free_molecular():
+    """Slip of a diffuse wall lowers the damping, from no effect in the continuum limit (tau*omega
+    -> 0, no slip) monotonically towards the free-molecular ratio 1/2 (F^BB = 2 F^DS, pinned exactly
+    above).  D2Q37-H2 plate, gamma_bar(DS)/gamma_bar(BB) at tau*omega = 0.01, 0.1, 1.  (The paper
+    prints a reduction of 0 - 0.4 over its cases; for this discretization the plate at tau*omega = 1
+    gives 0.53, recorded as a discrepancy in the design notes.)"""
+    Q, nx, ny = 37, 2, 120
+    lab = orc.geometry_plate(Q, nx, ny)
+    ratios = []
+    for to in (0.01, 0.1, 1.0):
+        tau, omega, P = orc.params_from_tau_omega(Q, to)
+        res = {}
+        for wall in (orc.WALL_BB, orc.WALL_DS):
+            _, F = orc.run(Q, lab, tau, omega, 1e-3, 4 * P, collision=orc.COLL_REG, drive=orc.DRIVE_WALL, wall=wall)
+            res[wall], _ = orc.in_phase_quadrature(F[:, 0], omega, orc.DRIVE_WALL, skip=2 * P)
+        ratios.append(res[orc.WALL_DS] / res[orc.WALL_BB])
+    assert ratios[0] > 0.95
+    assert ratios[0] > ratios[1] > ratios[2] > 0.4, ratios
