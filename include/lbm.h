@@ -51,6 +51,14 @@ enum { LBM_DRIVE_WALL = 0, LBM_DRIVE_BODYFORCE = 1 };
 enum { LBM_COLL_BGK = 0, LBM_COLL_REGULARIZED = 1 };
 enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16 = 3 };
 
+/* Gas-wall interaction (lbm_geometry.wall_scheme).  Bounce-back (Eq. 12): a population sent into
+ * a wall comes back reversed, plus 2 w_i rho0 c_i.U_w / theta for a moving wall (no slip).
+ * Diffuse scattering (Eq. 11): the populations a wall returns to a node along its blocked links are
+ * the wall's discrete Maxwellian (the equilibrium of the run's order at the wall velocity), with
+ * the density that returns exactly the mass the node sent into that wall (fully accommodating
+ * surface; the gas slips).  In free-molecular flow the diffuse force is half the bounce-back one. */
+enum { LBM_SCHEME_BOUNCEBACK = 0, LBM_SCHEME_DIFFUSE = 1 };
+
 /* Node labels of a geometry (LBM_GEOM_MASK input, lbm_get_labels output). */
 enum { LBM_FLUID = 0, LBM_BODY = 1, LBM_WALL = 2 };
 
@@ -70,6 +78,7 @@ typedef struct {
     int collision;             /* LBM_COLL_REGULARIZED (Eqs. 18-19) or LBM_COLL_BGK (Eq. 14)      */
     int storage;               /* LBM_STORE_*: population storage type; arithmetic is FP64 for F64
                                   and FP32 otherwise; the force is accumulated in FP64              */
+    int wall_scheme;           /* LBM_SCHEME_BOUNCEBACK (0, default) or LBM_SCHEME_DIFFUSE          */
 } lbm_geometry;
 
 /*

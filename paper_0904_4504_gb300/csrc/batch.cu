@@ -290,6 +290,8 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     if (d->lattice != b->Q || d->geom.storage != b->storage || d->geom.collision != b->collision)
         return set_error(LBM_EINVAL, "instance lattice/storage/collision differ from the batch's");
     if (d->nsteps < 1) return set_error(LBM_EINVAL, "nsteps must be >= 1");
+    if (b->mode == LBM_BATCH_PERSISTENT && d->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
+        return set_error(LBM_EINVAL, "the persistent batch kernel is built for bounce-back walls only");
     HostLattice H;
     host_lattice(d->lattice, H);
     const size_t bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->nsteps, b->bx, b->by);

@@ -86,6 +86,9 @@ static int encode_map(CUtensorMap* map, void* base, int storage, int nx, int ny,
 }
 
 void* find_launcher_q9(int storage, int coll, bool batched);
+void* find_launcher_q9_ds(int storage, int coll);
+void* find_launcher_q37_wide_ds(int storage, int coll);
+void* find_launcher_q37_half_ds(int storage, int coll);
 void* find_launcher_q37_wide(int storage, int coll, bool batched);
 void* find_launcher_q37_half(int storage, int coll, bool batched);
 
@@ -96,8 +99,13 @@ static void* find_launcher(int Q, int storage, int coll, bool batched) {
     return nullptr;
 }
 
-StepLaunchFn find_step_launcher(int Q, int storage, int coll) {
-    return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
+StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall) {
+    if (wall == 0) return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
+    void* f = nullptr;
+    if (Q == 9) f = find_launcher_q9_ds(storage, coll);
+    else if (Q == 37 && storage <= ST_F32) f = find_launcher_q37_wide_ds(storage, coll);
+    else if (Q == 37) f = find_launcher_q37_half_ds(storage, coll);
+    return reinterpret_cast<StepLaunchFn>(f);
 }
 BatchKernelFn find_batch_kernel(int Q, int storage, int coll) {
     return find_launcher(Q, storage, coll, true);
@@ -578,12 +586,14 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     if (lattice == LBM_D2Q9 && g.eq_order != 2) return set_error(LBM_EINVAL, "D2Q9 supports eq_order 2 only");
     if (g.collision != LBM_COLL_BGK && g.collision != LBM_COLL_REGULARIZED)
         return set_error(LBM_EINVAL, "bad collision");
+    if (g.wall_scheme != LBM_SCHEME_BOUNCEBACK && g.wall_scheme != LBM_SCHEME_DIFFUSE)
+        return set_error(LBM_EINVAL, "bad wall scheme %d", g.wall_scheme);
     const size_t es = storage_size(g.storage);
     if (!es) return set_error(LBM_EINVAL, "bad storage type %d", g.storage);
     if (es == 2 && !(g.u0 > 0.0))
         return set_error(LBM_EINVAL, "16-bit storage is scaled by u0 and needs u0 > 0");
-    StepLaunchFn fn = find_step_launcher(lattice, g.storage, g.collision);
-    if (!fn) return set_error(LBM_EINVAL, "no kernel for this lattice/storage/collision");
+    StepLaunchFn fn = find_step_launcher(lattice, g.storage, g.collision, g.wall_scheme);
+    if (!fn) return set_error(LBM_EINVAL, "no kernel for this lattice/storage/collision/wall");
 
     lbm_sim* s = new (std::nothrow) lbm_sim();
     if (!s) return set_error(LBM_ENOMEM, "host allocation");
@@ -666,6 +676,7 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.pitch = s->pitch;
     d.eq_order = g.eq_order;
     d.moving = g.drive == LBM_DRIVE_WALL;
+    d.wall_ds = g.wall_scheme == LBM_SCHEME_DIFFUSE;
     d.body_force = g.drive == LBM_DRIVE_BODYFORCE;
     d.rho0 = g.rho0;
     d.s = es == 2 ? g.u0 : 1.0;
@@ -705,6 +716,8 @@ int lbm_set_variant(lbm_sim* s, int variant) {
     int rc = check_sim(s);
     if (rc) return rc;
     if (variant == 0) return lbm_set_tile(s, s->plain_bx, s->plain_by);
+    if (s->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
+        return set_error(LBM_EINVAL, "staged variants are built for bounce-back walls only");
     int bx, by, bw, pad;
     TmaStepLaunchFn fn = find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
     if (!fn || !variant_tile(variant, &bx, &by))
@@ -899,7 +912,7 @@ int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
     std::vector<lbm_tune_entry> cand;
     for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
     for (int v : variants)
-        if (find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, v)) {
+        if (s->geom.wall_scheme == LBM_SCHEME_BOUNCEBACK && find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, v)) {
             int bx = 0, by = 0;
             variant_tile(v, &bx, &by);
             cand.push_back(lbm_tune_entry{v, bx, by, 0.0});

@@ -71,7 +71,7 @@ extern "C" int lbm_step_noalloc(const lbm_sim* sim, long n, const void* g_in, vo
     const cudaError_t arc = scratch_address(v.device, &base);
     if (arc != cudaSuccess || !base)
         return set_error(LBM_ECUDA, "cudaGetSymbolAddress of the step scratch: %s", cudaGetErrorString(arc));
-    StepLaunchFn fn = find_step_launcher(v.Q, v.storage, v.collision);
+    StepLaunchFn fn = find_step_launcher(v.Q, v.storage, v.collision, v.inst.wall_ds);
     if (!fn) return set_error(LBM_EINVAL, "no kernel for this simulation");
 
     unsigned char* b = static_cast<unsigned char*>(base);

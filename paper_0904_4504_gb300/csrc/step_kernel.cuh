@@ -53,6 +53,7 @@ struct InstDev {
     int ntiles, nslots;
     int eq_order;                // 2 or 4
     int moving;                  // 1: body links carry the moving-wall term (wall drive)
+    int wall_ds;                 // 0: bounce-back (Eq. 12); 1: diffuse scattering (Eq. 11)
     int body_force;              // 1: fluid gets rho * g (body-frame drive)
     double rho0;
     double s, inv_s;             // storage scale
@@ -177,7 +178,7 @@ struct Coef {
 // Bounce-back (fix-up of h on blocked links), moments and collision coefficients of the fluid node
 // (x, y) whose pulled populations are in h.  Adds the momentum the node's blocked body links hand
 // to the body to (Fx, Fy).
-template <class L, class ST, int COLL>
+template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                         float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
                                         Coef<typename StoreT<ST>::CT>& C) {
@@ -198,7 +199,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
     }
     // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
     // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
-    if (cls == NODE_BOUNDARY) {
+    if (cls == NODE_BOUNDARY && WALL == 0) {
         const ulonglong2 lk = P.links[idx];
         const unsigned long long blk = lk.x | lk.y;
 #pragma unroll
@@ -218,6 +219,67 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
                 }
                 h[i] = own + (T)mw;
                 // the regularized path keeps h relative to the stream until the moments
+                if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
+            }
+        }
+    } else if (WALL == 1 && cls == NODE_BOUNDARY) {
+        // Eq. 11 on blocked links: each wall returns its discrete Maxwellian at the wall velocity,
+        // f_i = w_i rho_w (1 + e_i(U_w)), with rho_w set so that the node gets back exactly the mass
+        // it sends into that wall (per wall: body = bits of .x, static wall = bits of .y)
+        const ulonglong2 lk = P.links[idx];
+        const unsigned long long blk = lk.x | lk.y;
+        const T rho0 = kconst<T>(P.rho0, P.rho0_f), sT = kconst<T>(P.s, P.s_f);
+        const T Ub = P.moving ? kconst<T>(dv, dv_f) : (T)0;
+        const T ith = (T)(1.0 / L::theta()), bb = Ub * Ub * ith;
+        const bool eq4 = P.eq_order >= 4;
+        T in[2] = {0, 0}, mw[2] = {0, 0}, se[2] = {0, 0};
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if ((blk >> i) & 1ull) {
+                const int wb = ((lk.x >> i) & 1ull) ? 0 : 1;
+                T own = S::ld(src + opp_of<L>(i) * plane + idx);
+                if (off) own += (T)P.Hl[opp_of<L>(i)];
+                h[i] = own;  // kept until the second pass
+                const T w = (T)w_of<L>(i);
+                in[wb] += w * own;
+                mw[wb] += w;
+                if (wb == 0) {
+                    const T a = (T)cx_of<L>(i) * Ub * ith;
+                    T e = a + (T)0.5 * (a * a - bb);
+                    if (eq4) e += (a * a * a - (T)3 * a * bb) * (T)(1.0 / 6.0) +
+                                  (a * a * a * a - (T)6 * a * a * bb + (T)3 * bb * bb) * (T)(1.0 / 24.0);
+                    se[0] += w * e;
+                }
+            }
+        }
+        T drw[2], rw[2];  // rho_w - rho0 and rho_w of each wall
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const T den = mw[k] + se[k];
+            drw[k] = den > (T)0 ? (sT * in[k] - rho0 * se[k]) / den : (T)0;
+            rw[k] = rho0 + drw[k];
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if ((blk >> i) & 1ull) {
+                const int cx = cx_of<L>(i), cy = cy_of<L>(i);
+                const bool body = (lk.x >> i) & 1ull;
+                const int wb = body ? 0 : 1;
+                T e = 0;
+                if (body) {
+                    const T a = (T)cx * Ub * ith;
+                    e = a + (T)0.5 * (a * a - bb);
+                    if (eq4) e += (a * a * a - (T)3 * a * bb) * (T)(1.0 / 6.0) +
+                                  (a * a * a * a - (T)6 * a * a * bb + (T)3 * bb * bb) * (T)(1.0 / 24.0);
+                }
+                const T hadv = (drw[wb] + rw[wb] * e) / sT;
+                if (body) {
+                    const double hs = (double)h[i] + (double)hadv;
+                    const double ws = w_of<L>(i) * P.s;
+                    Fx -= cx * ws * hs;
+                    Fy -= cy * ws * hs;
+                }
+                h[i] = hadv;
                 if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
             }
         }
@@ -339,7 +401,7 @@ __device__ __forceinline__ void eval_pair(const Coef<T>& C, int k, T hp, T hm, T
 }
 
 // prepare + evaluation + store of one node.
-template <class L, class ST, int COLL>
+template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
                                               double dv, float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx,
                                               double& Fy) {
@@ -349,7 +411,7 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     const long long plane = P.plane;
     const int idx = y * P.pitch + x;
     Coef<T> C;
-    prepare<L, ST, COLL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
+    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
     const bool off = sizeof(ST) == 2 && P.stream_off;
     S::st(dst + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)P.Hs[0] : (T)0));
 #pragma unroll
@@ -365,13 +427,15 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     }
 }
 
-// Advection + bounce-back + collision of the fluid node (x, y), sources from global memory.
-template <class L, class ST, int COLL>
+// Advection + wall + collision of the fluid node (x, y), sources from global memory.  WALL selects
+// bounce-back (0) or diffuse scattering (1) at compile time: the diffuse fix-up costs registers
+// that the bulk of the nodes must not pay for.
+template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void node_update(const InstDev& P, const void* src, void* dst, int x, int y, int cls,
                                             double dv, float dv_f, double& Fx, double& Fy) {
     typename StoreT<ST>::CT h[L::Q];
     gather_global<L, ST>(P, static_cast<const ST*>(src), x, y, h);
-    collide_store<L, ST, COLL>(P, src, dst, x, y, cls, dv, dv_f, h, Fx, Fy);
+    collide_store<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, h, Fx, Fy);
 }
 
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
@@ -428,7 +492,7 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
 }
 
 // One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
-template <class L, class ST, int COLL>
+template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const void* src, void* dst, double dv,
                                              float dv_f, double2* force_out) {
     const int tx = tile % P.ntx, ty = tile / P.ntx;
@@ -436,14 +500,14 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
     const int y = ty * blockDim.y + threadIdx.y;
     double Fx = 0.0, Fy = 0.0;
     const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-    if (cls != NODE_SOLID) node_update<L, ST, COLL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
+    if (cls != NODE_SOLID) node_update<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
     tile_epilogue(P, tile, force_out, Fx, Fy);
 }
 
 // Single-instance step: one block per tile.
-template <class L, class ST, int COLL>
+template <class L, class ST, int COLL, int WALL = 0>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
-    process_tile<L, ST, COLL>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
+    process_tile<L, ST, COLL, WALL>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
 // One instance of a batch: its step-kernel parameters plus what changes from step to step.
@@ -522,14 +586,14 @@ __global__ void __launch_bounds__(128, 5) batch_kernel(const BatchInst* __restri
 using StepLaunchFn = cudaError_t (*)(const InstDev& P, dim3 block, cudaStream_t stream);
 using BatchKernelFn = const void*;
 
-template <class L, class ST, int COLL>
+template <class L, class ST, int COLL, int WALL = 0>
 cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
-    step_kernel<L, ST, COLL><<<P.ntiles, block, 0, stream>>>(P);
+    step_kernel<L, ST, COLL, WALL><<<P.ntiles, block, 0, stream>>>(P);
     return cudaGetLastError();
 }
 
 // Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.
-StepLaunchFn find_step_launcher(int Q, int storage, int coll);
+StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall = 0);
 // Address of batch_kernel<...> for a cooperative launch (nullptr if not built).
 BatchKernelFn find_batch_kernel(int Q, int storage, int coll);
 

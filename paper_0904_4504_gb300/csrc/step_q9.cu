@@ -22,6 +22,30 @@ void* find_launcher_q9(int storage, int coll, bool batched) {
     }
 }
 
+// Plain step kernel with diffuse-scattering walls.
+void* find_launcher_q9_ds(int storage, int coll) {
+    switch (storage * 2 + coll) {
+        case ST_F64 * 2 + COLL_BGK:
+            return (void*)&launch_step<D2Q9, double, COLL_BGK, 1>;
+        case ST_F64 * 2 + COLL_REG:
+            return (void*)&launch_step<D2Q9, double, COLL_REG, 1>;
+        case ST_F32 * 2 + COLL_BGK:
+            return (void*)&launch_step<D2Q9, float, COLL_BGK, 1>;
+        case ST_F32 * 2 + COLL_REG:
+            return (void*)&launch_step<D2Q9, float, COLL_REG, 1>;
+        case ST_BF16 * 2 + COLL_BGK:
+            return (void*)&launch_step<D2Q9, __nv_bfloat16, COLL_BGK, 1>;
+        case ST_BF16 * 2 + COLL_REG:
+            return (void*)&launch_step<D2Q9, __nv_bfloat16, COLL_REG, 1>;
+        case ST_F16 * 2 + COLL_BGK:
+            return (void*)&launch_step<D2Q9, __half, COLL_BGK, 1>;
+        case ST_F16 * 2 + COLL_REG:
+            return (void*)&launch_step<D2Q9, __half, COLL_REG, 1>;
+        default:
+            return nullptr;
+    }
+}
+
 // Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10, 11, 12 = one
 // node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 20, 21, 22 = two nodes per thread on 64 x 4,
 // 64 x 2, 128 x 2 tiles.

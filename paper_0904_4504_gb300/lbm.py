@@ -30,6 +30,7 @@ LBM_COLL_BGK, LBM_COLL_REGULARIZED = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = 0, 1, 2, 3
 LBM_FLUID, LBM_BODY, LBM_WALL = 0, 1, 2
 LBM_BATCH_STREAMS, LBM_BATCH_PERSISTENT = 0, 1
+LBM_SCHEME_BOUNCEBACK, LBM_SCHEME_DIFFUSE = 0, 1
 STORAGE_BYTES = {LBM_STORE_F64: 8, LBM_STORE_F32: 4, LBM_STORE_BF16: 2, LBM_STORE_F16: 2}
 
 
@@ -51,6 +52,7 @@ class lbm_geometry(ctypes.Structure):
         ("eq_order", ctypes.c_int),
         ("collision", ctypes.c_int),
         ("storage", ctypes.c_int),
+        ("wall_scheme", ctypes.c_int),
     ]
 
 
@@ -246,9 +248,9 @@ def lbm_params_from_tau_omega(lattice: int, tau_omega: float, delta_min: float =
 
 
 def make_geometry(kind=LBM_GEOM_NONE, lx=0, ly=0, drive=LBM_DRIVE_WALL, u0=0.0, rho0=1.0, mask=None, eq_order=2,
-                  collision=LBM_COLL_REGULARIZED, storage=LBM_STORE_F32):
+                  collision=LBM_COLL_REGULARIZED, storage=LBM_STORE_F32, wall_scheme=LBM_SCHEME_BOUNCEBACK):
     """An lbm_geometry; `mask` (ny x nx uint8) is kept alive on the returned object."""
-    g = lbm_geometry(kind, lx, ly, drive, u0, rho0, None, eq_order, collision, storage)
+    g = lbm_geometry(kind, lx, ly, drive, u0, rho0, None, eq_order, collision, storage, wall_scheme)
     if mask is not None:
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         g._mask_ref = m

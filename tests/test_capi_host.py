@@ -89,3 +89,10 @@ def test_batch_create_rejects_bad_arguments():
     assert e.value.code == L.LBM_EINVAL
     assert L.lib().lbm_batch_run(None, 1) == L.LBM_EINVAL
     L.lib().lbm_batch_destroy(None)
+
+
+def test_create_rejects_bad_wall_scheme():
+    geom = L.make_geometry(kind=L.LBM_GEOM_NONE, u0=1e-3, wall_scheme=5)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create(37, 64, 64, 0.8, 0.1, geom)
+    assert e.value.code == L.LBM_EINVAL and "wall scheme" in L.lbm_last_error()

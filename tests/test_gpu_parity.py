@@ -46,10 +46,10 @@ ROUND16 = {L.LBM_STORE_BF16: 2.0 ** -8, L.LBM_STORE_F16: 2.0 ** -11}
 
 def run_both(Q, nx, ny, tau, omega, kind, steps, *, lx=0, ly=0, mask=None, drive=L.LBM_DRIVE_WALL, u0=1e-3,
              eq_order=2, collision=L.LBM_COLL_REGULARIZED, storage=L.LBM_STORE_F64, init_exp=None, seed=0,
-             tile=None, n0_chunks=1):
+             tile=None, n0_chunks=1, wall=L.LBM_SCHEME_BOUNCEBACK):
     """Run `steps` steps on the GPU and on the oracle; returns (g_gpu, g_or, F_gpu, F_or, labels, g0)."""
     geom = L.make_geometry(kind=kind, lx=lx, ly=ly, drive=drive, u0=u0, mask=mask, eq_order=eq_order,
-                           collision=collision, storage=storage)
+                           collision=collision, storage=storage, wall_scheme=wall)
     lab_or = oracle_labels(kind, Q, nx, ny, lx, ly, mask)
     s = 1.0 if L.STORAGE_BYTES[storage] > 2 else u0
     _, w, _ = L.lbm_lattice_velocities(Q)
@@ -77,7 +77,7 @@ def run_both(Q, nx, ny, tau, omega, kind, steps, *, lx=0, ly=0, mask=None, drive
         L.lbm_destroy(h)
     f0 = g_to_oracle_state(Q, g0) if g0 is not None else None
     f, F_or = orc.run(Q, lab_or, tau, omega, u0, steps, eq_order=eq_order, collision=collision, drive=drive, f=f0,
-                      nthreads=orc.max_threads())
+                      nthreads=orc.max_threads(), wall=wall)
     return g_gpu, oracle_state_to_g(Q, f), F_gpu, F_or, lab_or, g0
 
 
@@ -315,3 +315,56 @@ def test_full_size_momentum_balance_fp32():
         rhs = (M + P[k][1]) * gx - F[n, 0]
         bound = 4e-7 * max(abs(P[k][0]), abs(P[k + 1][0])) + 1e-5 * abs(F[n, 0])
         assert abs(lhs - rhs) <= bound, (lhs, rhs, bound)
+
+
+# -------------------------------------------------------------------------------------------------
+# diffuse-scattering walls (Eq. 11)
+# -------------------------------------------------------------------------------------------------
+
+DS_CASES = [
+    ("q37-reg-h4-beam-body-f64", 37, 70, 41, L.LBM_GEOM_BEAM, 12, 9, L.LBM_DRIVE_BODYFORCE, 4,
+     L.LBM_COLL_REGULARIZED, L.LBM_STORE_F64, 25),
+    ("q37-reg-h2-plate-wall-f64", 37, 45, 50, L.LBM_GEOM_PLATE, 0, 0, L.LBM_DRIVE_WALL, 2, L.LBM_COLL_REGULARIZED,
+     L.LBM_STORE_F64, 25),
+    ("q9-bgk-plate-wall-f64", 9, 45, 37, L.LBM_GEOM_PLATE, 0, 0, L.LBM_DRIVE_WALL, 2, L.LBM_COLL_BGK,
+     L.LBM_STORE_F64, 30),
+    ("q37-reg-h4-mask-wall-f32", 37, 67, 53, L.LBM_GEOM_MASK, 0, 0, L.LBM_DRIVE_WALL, 4, L.LBM_COLL_REGULARIZED,
+     L.LBM_STORE_F32, 25),
+    ("q37-bgk-h4-beam-body-f32", 37, 70, 41, L.LBM_GEOM_BEAM, 12, 9, L.LBM_DRIVE_BODYFORCE, 4, L.LBM_COLL_BGK,
+     L.LBM_STORE_F32, 25),
+]
+
+
+@pytest.mark.parametrize("case", DS_CASES, ids=[c[0] for c in DS_CASES])
+def test_parity_diffuse_walls(case):
+    name, Q, nx, ny, kind, lx, ly, drive, eq, coll, st, steps = case
+    mask = I.random_mask(nx, ny, 3 if Q == 37 else 1, seed=7) if kind == L.LBM_GEOM_MASK else None
+    g_gpu, g_or, F_gpu, F_or, lab, g0 = run_both(Q, nx, ny, 0.83, 0.05, kind, steps, lx=lx, ly=ly, mask=mask,
+                                                 drive=drive, u0=2e-3, eq_order=eq, collision=coll, storage=st,
+                                                 init_exp=-17, seed=13, n0_chunks=2, wall=L.LBM_SCHEME_DIFFUSE)
+    assert_state_close(Q, g_gpu, g_or, lab, st, steps, g0)
+    assert_force_close(F_gpu, F_or, Q, lab, st, steps)
+
+
+@pytest.mark.parametrize("st", [L.LBM_STORE_F16, L.LBM_STORE_BF16])
+def test_parity_diffuse_16bit_one_step(st):
+    Q, nx, ny = 37, 70, 41
+    g_gpu, g_or, F_gpu, F_or, lab, g0 = run_both(Q, nx, ny, 0.9, 0.05, L.LBM_GEOM_BEAM, 1, lx=12, ly=9,
+                                                 drive=L.LBM_DRIVE_BODYFORCE, u0=2e-3, eq_order=4,
+                                                 collision=L.LBM_COLL_REGULARIZED, storage=st, init_exp=-7, seed=5,
+                                                 wall=L.LBM_SCHEME_DIFFUSE)
+    assert_state_close(Q, g_gpu, g_or, lab, st, 1, g0, 2e-3 * stream_offset_magnitude(Q, 2e-3, 0.05, 1, 4))
+    assert_force_close(F_gpu, F_or, Q, lab, st, 1)
+
+
+def test_diffuse_rejected_by_staged_variants():
+    geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=12, ly=9, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
+                           storage=L.LBM_STORE_F32, wall_scheme=L.LBM_SCHEME_DIFFUSE)
+    h = L.lbm_create(37, 200, 90, 0.9, 0.05, geom)
+    try:
+        with pytest.raises(L.LbmError):
+            L.lbm_set_variant(h, 11)
+        L.lbm_step(h, 3)
+        L.lbm_synchronize(h)
+    finally:
+        L.lbm_destroy(h)
