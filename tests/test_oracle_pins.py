@@ -4,7 +4,8 @@ Each test checks the oracle against something other than itself: Gaussian moment
 property the paper requires of the lattice, Sec. 5), Maxwellian moments of the equilibrium (Eqs. 8,
 9, 15), the algebra of the projection (Eq. 19), exact conservation laws, the Chapman-Enskog viscosity
 nu = theta (tau - 1/2) (Sec. 6, "tau = mu/p = nu/theta"), the quasi-steady Couette closed form, the
-Stokes second problem (Eq. 4), and the lattice free-molecular force (Sec. 4.1, Eq. 13).  The
+Stokes second problem (Eq. 4), the lattice free-molecular force (Sec. 4.1, Eq. 13), and the
+Galilean equivalence of the moving-wall (lab) and body-force (body) frames.  The
 closed forms are written out here from the mathematics, not taken from the oracle.
 """
 import math
@@ -383,10 +384,11 @@ def test_free_molecular_diffuse_plate_is_half_bounce_back(Q):
 
 def test_diffuse_slip_reduction_goes_from_continuum_to_free_molecular():
     """Slip of a diffuse wall lowers the damping, from no effect in the continuum limit (tau*omega
-    -> 0, no slip) monotonically towards the free-molecular ratio 1/2 (F^BB = 2 F^DS, pinned exactly
-    above).  D2Q37-H2 plate, gamma_bar(DS)/gamma_bar(BB) at tau*omega = 0.01, 0.1, 1.  (The paper
-    prints a reduction of 0 - 0.4 over its cases; for this discretization the plate at tau*omega = 1
-    gives 0.53, recorded as a discrepancy in the design notes.)"""
+    -> 0, no slip) monotonically down to about the free-molecular ratio 1/2 (F^BB = 2 F^DS, pinned
+    exactly above).  D2Q37-H2 plate, gamma_bar(DS)/gamma_bar(BB) at tau*omega = 0.01, 0.1, 1
+    (0.975, 0.836, 0.471).  (The paper prints a reduction of 0 - 0.4 over its cases; for this
+    discretization the plate at tau*omega = 1 shows a reduction of 0.53, recorded as a discrepancy
+    in the design notes.)"""
     Q, nx, ny = 37, 2, 120
     lab = orc.geometry_plate(Q, nx, ny)
     ratios = []
@@ -399,3 +401,34 @@ def test_diffuse_slip_reduction_goes_from_continuum_to_free_molecular():
         ratios.append(res[orc.WALL_DS] / res[orc.WALL_BB])
     assert ratios[0] > 0.95
     assert ratios[0] > ratios[1] > ratios[2] > 0.4, ratios
+
+
+# ------------------------------------------------------------------------------------------------
+# lab frame (moving wall, Sec. 6) against body frame (body force): Galilean equivalence
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau_omega", [0.1, 1.0, 10.0])
+def test_lab_and_body_frames_agree_up_to_half_a_step(tau_omega):
+    """Two independent mechanisms drive the same flow.  In a periodic box, u_B = u_L - V with the
+    same periodic pressure turns the linear Stokes problem of a body moving with V(t) into the one of
+    a fixed body in fluid pushed by the force density -rho dV/dt, so the force on the body is the
+    same function of time (no Froude-Krylov term: the uniform force takes the place of the pressure
+    ramp that an unbounded domain would need).  On the lattice the body-frame momentum exchange of
+    step n carries the populations collided at step n - 1/2 against n + 1/2 for the moving-wall
+    term, so the two histories match after a half-step time shift, i.e. a rotation of (F_in, F_q)
+    by omega/2.  The unshifted quadrature differs by about omega/2 of the amplitude (> 1e-2 here), so
+    a wrong wall term, drive sign or force stamp fails this pin."""
+    Q, n, b = 37, 64, 8
+    tau, om, P = orc.params_from_tau_omega(Q, tau_omega)
+    lab = orc.geometry_beam(n, n, b, b)
+    fits = {}
+    for drive in (orc.DRIVE_WALL, orc.DRIVE_BODY):
+        _, F = orc.run(Q, lab, tau, om, 1e-3, 6 * P, eq_order=4, drive=drive, nthreads=orc.max_threads())
+        fits[drive] = orc.in_phase_quadrature(F[:, 0], om, drive, skip=3 * P)
+    li, lq = fits[orc.DRIVE_WALL]
+    bi, bq = fits[orc.DRIVE_BODY]
+    amp = math.hypot(li, lq)
+    c, s = math.cos(om / 2), math.sin(om / 2)
+    assert abs(lq - bq) > 1e-2 * amp
+    assert abs(li - (bi * c - bq * s)) < 3e-4 * amp
+    assert abs(lq - (bq * c + bi * s)) < 3e-4 * amp
