@@ -59,6 +59,16 @@ enum { LBM_STORE_F64 = 0, LBM_STORE_F32 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16 =
  * surface; the gas slips).  In free-molecular flow the diffuse force is half the bounce-back one. */
 enum { LBM_SCHEME_BOUNCEBACK = 0, LBM_SCHEME_DIFFUSE = 1 };
 
+/* Population storage layout (lbm_geometry.layout).  LBM_LAYOUT_AB: two buffers, each step pulls
+ * from one into the other (Eq. 17).  LBM_LAYOUT_AA: one buffer updated in place; even steps pull
+ * from the neighbours and push to them, odd steps read and write only the node itself (the "AA"
+ * pattern).  Same results up to the rounding of the storage type; half the population memory.
+ * AA runs the plain kernel only (lbm_set_variant 0) with bounce-back walls and is not available in
+ * the persistent batch mode; lbm_get_state / lbm_set_state need an even number of steps done
+ * (LBM_ERANGE otherwise).  lbm_step_noalloc always runs the two-buffer step on the caller's
+ * buffers, whatever the simulation's layout. */
+enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 };
+
 /* Node labels of a geometry (LBM_GEOM_MASK input, lbm_get_labels output). */
 enum { LBM_FLUID = 0, LBM_BODY = 1, LBM_WALL = 2 };
 
@@ -79,6 +89,7 @@ typedef struct {
     int storage;               /* LBM_STORE_*: population storage type; arithmetic is FP64 for F64
                                   and FP32 otherwise; the force is accumulated in FP64              */
     int wall_scheme;           /* LBM_SCHEME_BOUNCEBACK (0, default) or LBM_SCHEME_DIFFUSE          */
+    int layout;                /* LBM_LAYOUT_AB (0, default) or LBM_LAYOUT_AA                       */
 } lbm_geometry;
 
 /*
@@ -157,6 +168,7 @@ typedef struct {
     int block_x, block_y;        /* tile shape of the step kernel                                  */
     size_t h2d_bytes, d2h_bytes; /* host<->device bytes copied by the library so far               */
     int variant;                 /* step kernel in use, see lbm_set_variant                        */
+    int layout;                  /* LBM_LAYOUT_AB or LBM_LAYOUT_AA                                 */
 } lbm_info_t;
 
 int lbm_info(lbm_sim* sim, lbm_info_t* out);
@@ -167,7 +179,9 @@ int lbm_info(lbm_sim* sim, lbm_info_t* out);
 int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
 
 /* Choose the step kernel.  0: plain kernel, one block per tile of lbm_set_tile's shape, wrapped
- * global loads (the default).  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
+ * global loads (the default).  1, 2: the plain kernel on 32 x 4 tiles compiled for at least 6 (1)
+ * or 7 (2) resident blocks per SM (fewer registers, more warps to hide load latency; D2Q37,
+ * FP32/BF16/FP16 storage).  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
  * copied to shared memory by bulk tensor copies (TMA), one box per direction plane:
  * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
  * 20, 21, 22: two neighbouring nodes per thread (paired loads and stores), tiles of 64 x 4,

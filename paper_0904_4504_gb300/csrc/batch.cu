@@ -108,14 +108,15 @@ void free_graph(lbm_batch* b) {
 }
 
 // Device bytes of one instance (populations, geometry arrays, force history, drive table).
-size_t footprint(const HostLattice& H, int nx, int ny, int storage, long nsteps, int bx, int by) {
+size_t footprint(const HostLattice& H, int nx, int ny, int storage, int layout, long nsteps, int bx, int by) {
     const size_t es = storage_size(storage);
     const size_t align = 128 / es;
     const size_t pitch = (nx + align - 1) / align * align;
     const size_t plane = (size_t)ny * pitch;
     const size_t tiles = (size_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by);
     const size_t hist = std::max<size_t>(1024, (size_t)nsteps);
-    return 2 * plane * H.Q * es + plane * (1 + sizeof(ulonglong2)) + tiles * (sizeof(int) + sizeof(double2)) +
+    const size_t nbuf = layout == LBM_LAYOUT_AA ? 1 : 2;
+    return nbuf * plane * H.Q * es + plane * (1 + sizeof(ulonglong2)) + tiles * (sizeof(int) + 2 * sizeof(double2)) +
            hist * sizeof(double2) + (size_t)nsteps * (sizeof(double) + sizeof(float)) + 4096;
 }
 
@@ -279,7 +280,7 @@ int lbm_batch_footprint(const lbm_instance_desc* d, size_t* bytes) {
     if (!host_lattice(d->lattice, H)) return set_error(LBM_EINVAL, "unknown lattice %d", d->lattice);
     if (!storage_size(d->geom.storage)) return set_error(LBM_EINVAL, "bad storage type");
     if (d->nx < 1 || d->ny < 1 || d->nsteps < 0) return set_error(LBM_EINVAL, "bad size");
-    *bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->nsteps, 32, 4);
+    *bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->geom.layout, d->nsteps, 32, 4);
     return LBM_OK;
 }
 
@@ -292,9 +293,11 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     if (d->nsteps < 1) return set_error(LBM_EINVAL, "nsteps must be >= 1");
     if (b->mode == LBM_BATCH_PERSISTENT && d->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
         return set_error(LBM_EINVAL, "the persistent batch kernel is built for bounce-back walls only");
+    if (b->mode == LBM_BATCH_PERSISTENT && d->geom.layout != LBM_LAYOUT_AB)
+        return set_error(LBM_EINVAL, "the persistent batch kernel runs the two-buffer layout only");
     HostLattice H;
     host_lattice(d->lattice, H);
-    const size_t bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->nsteps, b->bx, b->by);
+    const size_t bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->geom.layout, d->nsteps, b->bx, b->by);
     if (b->used + bytes > b->budget)
         return set_error(LBM_ENOMEM, "instance needs %zu bytes, %zu of the %zu-byte budget are free", bytes,
                          b->budget - b->used, b->budget);
@@ -317,7 +320,8 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
         rc = lbm_set_tile(sim, b->bx, b->by);
     if (rc) return undo(rc);
     clear_error();
-    if ((rc = sim_reserve(sim, (size_t)d->nsteps))) return undo(rc);
+    // (+1: an in-place even step also writes the force of the step after it)
+    if ((rc = sim_reserve(sim, (size_t)d->nsteps + 1))) return undo(rc);
     if ((rc = lbm_set_stream(sim, b->mode == LBM_BATCH_STREAMS ? b->sub[id % kSubStreams] : b->stream)))
         return undo(rc);
     // drive table: nsteps doubles followed by the same values as nsteps floats

@@ -40,6 +40,8 @@ static TmaStepLaunchFn find_tma_launcher(int Q, int storage, int coll, int varia
 // Tile of a staged variant (see lbm_set_variant); false for other variants.
 static bool variant_tile(int variant, int* bx, int* by) {
     switch (variant) {
+        case 1:
+        case 2:
         case 10: *bx = 32; *by = 4; return true;
         case 11: *bx = 64; *by = 2; return true;
         case 12: *bx = 64; *by = 4; return true;
@@ -96,6 +98,26 @@ static void* find_launcher(int Q, int storage, int coll, bool batched) {
     if (Q == 9) return find_launcher_q9(storage, coll, batched);
     if (Q == 37) return storage <= ST_F32 ? find_launcher_q37_wide(storage, coll, batched)
                                           : find_launcher_q37_half(storage, coll, batched);
+    return nullptr;
+}
+
+void* find_occ_launcher_q37_wide(int storage, int coll, int variant);
+void* find_occ_launcher_q37_half(int storage, int coll, int variant);
+
+StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant) {
+    if (Q != 37 || variant < 1 || variant > 2) return nullptr;
+    return reinterpret_cast<StepLaunchFn>(storage <= ST_F32 ? find_occ_launcher_q37_wide(storage, coll, variant)
+                                                            : find_occ_launcher_q37_half(storage, coll, variant));
+}
+
+StepLaunchFn find_aa_launcher_q9(int storage, int coll, int phase);
+StepLaunchFn find_aa_launcher_q37_wide(int storage, int coll, int phase);
+StepLaunchFn find_aa_launcher_q37_half(int storage, int coll, int phase);
+
+StepLaunchFn find_aa_launcher(int Q, int storage, int coll, int phase) {
+    if (Q == 9) return find_aa_launcher_q9(storage, coll, phase);
+    if (Q == 37) return storage <= ST_F32 ? find_aa_launcher_q37_wide(storage, coll, phase)
+                                          : find_aa_launcher_q37_half(storage, coll, phase);
     return nullptr;
 }
 
@@ -375,8 +397,11 @@ struct lbm_sim {
     int variant = 0;                   // 0 plain kernel, else a staged variant (lbm_set_variant)
     bool stream_off = false;           // 16-bit body frame: store h - H(U(n)), see InstDev
     double U_stream = 0.0;             // U(n) = sum_{k<n} g(k + 1/2) for n = steps_done
-    StepLaunchFn launch = nullptr;
+    StepLaunchFn launch = nullptr;     // plain step in use (variant 0, or an occupancy variant 1-2)
+    StepLaunchFn launch_default = nullptr;
     TmaStepLaunchFn tma_launch = nullptr;
+    bool aa = false;                   // in-place single buffer (LBM_LAYOUT_AA)
+    StepLaunchFn aa_launch[2] = {nullptr, nullptr};  // even (pull-push) and odd (local) steps
     CUtensorMap maps[2];
     InstDev dev{};
 };
@@ -427,11 +452,13 @@ int setup_tiles(lbm_sim* s) {
     s->d_partials = nullptr;
     int rc = dev_alloc(s, &s->d_tile_slot, slot.size());
     if (rc) return rc;
-    rc = dev_alloc(s, &s->d_partials, (size_t)std::max(1, s->nslots));
+    // two force partials per slot: the in-place even step records the forces of two steps
+    const size_t np = 2 * (size_t)std::max(1, s->nslots);
+    rc = dev_alloc(s, &s->d_partials, np);
     if (rc) return rc;
     CUDA_TRY(cudaMemcpy(s->d_tile_slot, slot.data(), slot.size() * sizeof(int), cudaMemcpyHostToDevice));
     s->h2d_bytes += slot.size() * sizeof(int);
-    CUDA_TRY(cudaMemset(s->d_partials, 0, (size_t)std::max(1, s->nslots) * sizeof(double2)));
+    CUDA_TRY(cudaMemset(s->d_partials, 0, np * sizeof(double2)));
     s->dev.tile_slot = s->d_tile_slot;
     s->dev.partials = s->d_partials;
     s->dev.ntx = s->ntx;
@@ -448,8 +475,10 @@ int ensure_capacity(lbm_sim* s, size_t need) {
     CUDA_TRY(cudaMalloc((void**)&hist, cap * sizeof(double2)));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     CUDA_TRY(cudaMemset(hist, 0, cap * sizeof(double2)));
-    if (s->d_history && s->steps_done > 0)
-        CUDA_TRY(cudaMemcpy(hist, s->d_history, (size_t)s->steps_done * sizeof(double2), cudaMemcpyDeviceToDevice));
+    // an in-place even step has already written the force of the step after it
+    const size_t keep = std::min(s->cap, (size_t)s->steps_done + (s->aa ? 1 : 0));
+    if (s->d_history && keep > 0)
+        CUDA_TRY(cudaMemcpy(hist, s->d_history, keep * sizeof(double2), cudaMemcpyDeviceToDevice));
     cudaFree(s->d_history);
     s->device_bytes += (cap - s->cap) * sizeof(double2);
     s->d_history = hist;
@@ -514,6 +543,7 @@ SimView sim_view(const lbm_sim* s) {
     v.history = s->d_history;
     v.esize = s->esize;
     v.n_fluid = s->n_fluid;
+    v.aa = s->aa ? 1 : 0;
     return v;
 }
 
@@ -588,12 +618,21 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
         return set_error(LBM_EINVAL, "bad collision");
     if (g.wall_scheme != LBM_SCHEME_BOUNCEBACK && g.wall_scheme != LBM_SCHEME_DIFFUSE)
         return set_error(LBM_EINVAL, "bad wall scheme %d", g.wall_scheme);
+    if (g.layout != LBM_LAYOUT_AB && g.layout != LBM_LAYOUT_AA) return set_error(LBM_EINVAL, "bad layout %d", g.layout);
+    if (g.layout == LBM_LAYOUT_AA && g.wall_scheme != LBM_SCHEME_BOUNCEBACK)
+        return set_error(LBM_EINVAL, "the in-place (AA) layout is built for bounce-back walls only");
     const size_t es = storage_size(g.storage);
     if (!es) return set_error(LBM_EINVAL, "bad storage type %d", g.storage);
     if (es == 2 && !(g.u0 > 0.0))
         return set_error(LBM_EINVAL, "16-bit storage is scaled by u0 and needs u0 > 0");
     StepLaunchFn fn = find_step_launcher(lattice, g.storage, g.collision, g.wall_scheme);
     if (!fn) return set_error(LBM_EINVAL, "no kernel for this lattice/storage/collision/wall");
+    StepLaunchFn aa0 = nullptr, aa1 = nullptr;
+    if (g.layout == LBM_LAYOUT_AA) {
+        aa0 = find_aa_launcher(lattice, g.storage, g.collision, 0);
+        aa1 = find_aa_launcher(lattice, g.storage, g.collision, 1);
+        if (!aa0 || !aa1) return set_error(LBM_EINVAL, "no in-place kernel for this lattice/storage/collision");
+    }
 
     lbm_sim* s = new (std::nothrow) lbm_sim();
     if (!s) return set_error(LBM_ENOMEM, "host allocation");
@@ -605,6 +644,10 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     s->lat = H;
     s->esize = es;
     s->launch = fn;
+    s->launch_default = fn;
+    s->aa = g.layout == LBM_LAYOUT_AA;
+    s->aa_launch[0] = aa0;
+    s->aa_launch[1] = aa1;
     int rc = cudaGetDevice(&s->device) == cudaSuccess ? LBM_OK : LBM_ECUDA;
     if (rc) { delete s; return set_error(rc, "no CUDA device"); }
     rc = build_labels(lattice, nx, ny, g, s->labels);
@@ -635,7 +678,7 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
         }                       \
     } while (0)
 
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < (s->aa ? 1 : 2); ++b) {
         TRY_OR_FREE(dev_alloc(s, (char**)&s->buf[b], plane * H.Q * es));
         if (cudaMemset(s->buf[b], 0, plane * H.Q * es) != cudaSuccess) {
             free_sim(s);
@@ -709,6 +752,7 @@ int lbm_set_tile(lbm_sim* s, int block_x, int block_y) {
     s->plain_by = s->by = block_y;
     s->variant = 0;
     s->tma_launch = nullptr;
+    s->launch = s->launch_default;
     return setup_tiles(s);
 }
 
@@ -716,8 +760,20 @@ int lbm_set_variant(lbm_sim* s, int variant) {
     int rc = check_sim(s);
     if (rc) return rc;
     if (variant == 0) return lbm_set_tile(s, s->plain_bx, s->plain_by);
+    if (s->aa) return set_error(LBM_EINVAL, "the in-place (AA) layout runs the plain kernel (variant 0) only");
     if (s->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
-        return set_error(LBM_EINVAL, "staged variants are built for bounce-back walls only");
+        return set_error(LBM_EINVAL, "kernel variants are built for bounce-back walls only");
+    if (variant == 1 || variant == 2) {
+        StepLaunchFn f = find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
+        if (!f) return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        s->bx = 32;
+        s->by = 4;
+        s->variant = variant;
+        s->tma_launch = nullptr;
+        s->launch = f;
+        return setup_tiles(s);
+    }
     int bx, by, bw, pad;
     TmaStepLaunchFn fn = find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
     if (!fn || !variant_tile(variant, &bx, &by))
@@ -739,9 +795,32 @@ int lbm_step(lbm_sim* s, long n) {
     if (rc) return rc;
     if (n < 0) return set_error(LBM_EINVAL, "negative step count");
     if (n == 0) return LBM_OK;
-    rc = ensure_capacity(s, (size_t)(s->steps_done + n));
+    // an in-place even step also writes the force of the step after it
+    rc = ensure_capacity(s, (size_t)(s->steps_done + n + (s->aa ? 1 : 0)));
     if (rc) return rc;
     const dim3 block(s->bx, s->by);
+    if (s->aa) {
+        for (long k = 0; k < n; ++k) {
+            const int phase = (int)(s->steps_done & 1);
+            s->dev.src = s->buf[0];
+            s->dev.dst = s->buf[0];
+            s->dev.dv = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done);
+            s->dev.dv_f = (float)s->dev.dv;
+            s->dev.dv2 = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done + 1);
+            s->dev.dv2_f = (float)s->dev.dv2;
+            s->dev.stream_off = s->stream_off ? 1 : 0;
+            if (s->stream_off) {
+                stream_offset(s, s->U_stream, s->dev.Hl, s->dev.HM);
+                stream_offset(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+            }
+            s->dev.force_out = s->d_history + s->steps_done;
+            const cudaError_t e = s->aa_launch[phase](s->dev, block, s->stream);
+            if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
+            ++s->steps_done;
+            if (s->stream_off) s->U_stream += s->dev.dv;
+        }
+        return LBM_OK;
+    }
     for (long k = 0; k < n; ++k) {
         s->dev.src = s->buf[s->cur];
         s->dev.dst = s->buf[s->cur ^ 1];
@@ -855,6 +934,8 @@ int lbm_get_state(lbm_sim* s, double* out, size_t count) {
     if (rc && rc != LBM_ENONFINITE) return rc;
     const size_t N = (size_t)s->nx * s->ny, plane = (size_t)s->ny * s->pitch;
     if (!out || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
+    if (s->aa && (s->steps_done & 1))
+        return set_error(LBM_ERANGE, "the in-place layout holds the state after an even number of steps only");
     std::vector<unsigned char> host(plane * s->Q * s->esize);
     CUDA_TRY(cudaMemcpy(host.data(), s->buf[s->cur], host.size(), cudaMemcpyDeviceToHost));
     float H[37] = {0};
@@ -864,7 +945,9 @@ int lbm_get_state(lbm_sim* s, double* out, size_t count) {
         for (int y = 0; y < s->ny; ++y)
             for (int x = 0; x < s->nx; ++x) {
                 const size_t k = (size_t)y * s->nx + x;
-                const double v = to_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x);
+                // in place, after an even step count direction i sits in plane opp(i)
+                const int pi = s->aa ? s->lat.opp[i] : i;
+                const double v = to_double(host.data(), s->geom.storage, (size_t)pi * plane + (size_t)y * s->pitch + x);
                 // with the stream offset the kernel forms h = stored + H in FP32; do the same here
                 const double h = s->stream_off ? (double)(float)(v + H[i]) : v;
                 out[(size_t)i * N + k] = s->labels[k] ? 0.0 : scale * h;
@@ -878,6 +961,8 @@ int lbm_set_state(lbm_sim* s, const double* g, size_t count) {
     if (rc) return rc;
     const size_t N = (size_t)s->nx * s->ny, plane = (size_t)s->ny * s->pitch;
     if (!g || count != N * s->Q) return set_error(LBM_ERANGE, "need %zu values", N * s->Q);
+    if (s->aa && (s->steps_done & 1))
+        return set_error(LBM_ERANGE, "the in-place layout takes a state after an even number of steps only");
     std::vector<unsigned char> host(plane * s->Q * s->esize, 0);
     float H[37] = {0};
     if (s->stream_off) stream_offset(s, s->U_stream, H, nullptr);
@@ -887,7 +972,8 @@ int lbm_set_state(lbm_sim* s, const double* g, size_t count) {
             for (int x = 0; x < s->nx; ++x) {
                 const size_t k = (size_t)y * s->nx + x;
                 const double v = s->labels[k] ? 0.0 : g[(size_t)i * N + k] * inv - (double)H[i];
-                from_double(host.data(), s->geom.storage, (size_t)i * plane + (size_t)y * s->pitch + x, v);
+                const int pi = s->aa ? s->lat.opp[i] : i;
+                from_double(host.data(), s->geom.storage, (size_t)pi * plane + (size_t)y * s->pitch + x, v);
             }
     }
     CUDA_TRY(cudaMemcpy(s->buf[s->cur], host.data(), host.size(), cudaMemcpyHostToDevice));
@@ -908,11 +994,13 @@ int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
     if (steps < 1 || !n_out || (cap > 0 && !out)) return set_error(LBM_EINVAL, "need steps >= 1 and an output");
     // candidates: plain kernel tiles, then every staged variant built for this storage type
     const int tiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {32, 2}};
-    const int variants[] = {10, 11, 12, 20, 21, 22};
+    const int variants[] = {1, 2, 10, 11, 12, 20, 21, 22};
     std::vector<lbm_tune_entry> cand;
     for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
     for (int v : variants)
-        if (s->geom.wall_scheme == LBM_SCHEME_BOUNCEBACK && find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, v)) {
+        if (!s->aa && s->geom.wall_scheme == LBM_SCHEME_BOUNCEBACK &&
+            (find_tma_launcher(s->Q, s->geom.storage, s->geom.collision, v) ||
+             find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, v))) {
             int bx = 0, by = 0;
             variant_tile(v, &bx, &by);
             cand.push_back(lbm_tune_entry{v, bx, by, 0.0});
@@ -989,6 +1077,7 @@ int lbm_info(lbm_sim* s, lbm_info_t* o) {
     o->h2d_bytes = s->h2d_bytes;
     o->d2h_bytes = s->d2h_bytes;
     o->variant = s->variant;
+    o->layout = s->aa ? LBM_LAYOUT_AA : LBM_LAYOUT_AB;
     return LBM_OK;
 }
 

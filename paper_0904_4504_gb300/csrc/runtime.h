@@ -44,6 +44,7 @@ struct SimView {
     long steps_done;
     double2* history;
     size_t esize, n_fluid;
+    int aa;  // in-place single buffer (buf[1] is null)
 };
 SimView sim_view(const lbm_sim* s);
 // Make room for `steps` entries of force history (may allocate).

@@ -46,6 +46,7 @@ struct InstDev {
     double2* force_out;          // force on the body during this step (written by the last slot tile)
     int* err;                    // bit 0: non-finite force seen
     double dv;                   // drive of this step: U_w(n + 1/2) (wall) or g(n + 1/2) (body force)
+    double dv2;                  // drive of the next step, n + 3/2 (in-place AA streaming only)
     double2 fconst;              // geometry-only part of the force, -sum c_i 2 w_i rho0
     long long plane;             // ny * pitch
     int nx, ny, pitch;
@@ -63,7 +64,7 @@ struct InstDev {
     double mw_k;                 // 2 rho0 / (theta s): moving-wall term per unit c_i.U_w
     // FP32 copies of the constants above (and of dv), so that FP32 arithmetic converts nothing per
     // node: double -> float conversions run on the FP64 pipe, which is slow on this GPU
-    float dv_f, rho0_f, s_f, inv_s_f, omega_c_f, reg_a_f, src_k_f, pad_f;
+    float dv_f, rho0_f, s_f, inv_s_f, omega_c_f, reg_a_f, src_k_f, dv2_f;
     // 16-bit body-frame runs store h_i - H_i(n), with H_i(n) the (scaled) equilibrium deviation of
     // the uniform stream U(n) = sum_{k<n} g(k + 1/2) that the body force sets up; far from the body
     // the stored values are then small and so are their rounding errors.  Hl: H of the state read,
@@ -84,9 +85,10 @@ __device__ __forceinline__ float kconst<float>(double, float f) { return f; }
 
 template <class ST> struct StoreT;
 // Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
-// elements) with one access.
+// elements) with one access; rnd(v) is v rounded to the storage type (what a store and a load give).
 template <> struct StoreT<double> {
     using CT = double;
+    static __device__ __forceinline__ double rnd(double v) { return v; }
     static __device__ __forceinline__ double ld(const double* p) { return *p; }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
     static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
@@ -100,6 +102,7 @@ template <> struct StoreT<double> {
 };
 template <> struct StoreT<float> {
     using CT = float;
+    static __device__ __forceinline__ float rnd(float v) { return v; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
     static __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
@@ -113,6 +116,7 @@ template <> struct StoreT<float> {
 };
 template <> struct StoreT<__nv_bfloat16> {
     using CT = float;
+    static __device__ __forceinline__ float rnd(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
@@ -126,6 +130,7 @@ template <> struct StoreT<__nv_bfloat16> {
 };
 template <> struct StoreT<__half> {
     using CT = float;
+    static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
@@ -177,8 +182,13 @@ struct Coef {
 
 // Bounce-back (fix-up of h on blocked links), moments and collision coefficients of the fluid node
 // (x, y) whose pulled populations are in h.  Adds the momentum the node's blocked body links hand
-// to the body to (Fx, Fy).
-template <class L, class ST, int COLL, int WALL = 0>
+// to the body to (Fx, Fy).  OWN says where the node's own post-collision population opposite to
+// link i is: plane opp(i) of src (two buffers, OWN_OPP), plane i (in-place AA streaming, whose
+// even steps store directions swapped, OWN_SWAPPED), or nowhere because the wall rules were applied
+// when the populations were pushed (OWN_NONE: no fix-up here).
+enum OwnPlane { OWN_OPP = 0, OWN_SWAPPED = 1, OWN_NONE = 2 };
+
+template <class L, class ST, int COLL, int WALL = 0, int OWN = OWN_OPP>
 __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                         float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
                                         Coef<typename StoreT<ST>::CT>& C) {
@@ -199,14 +209,14 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
     }
     // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
     // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
-    if (cls == NODE_BOUNDARY && WALL == 0) {
+    if (cls == NODE_BOUNDARY && WALL == 0 && OWN != OWN_NONE) {
         const ulonglong2 lk = P.links[idx];
         const unsigned long long blk = lk.x | lk.y;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             if ((blk >> i) & 1ull) {
                 const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-                T own = S::ld(src + opp_of<L>(i) * plane + idx);
+                T own = S::ld(src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx);
                 if (off) own += (T)P.Hl[opp_of<L>(i)];
                 double mw = 0.0;
                 if ((lk.x >> i) & 1ull) {
@@ -222,7 +232,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
                 if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
             }
         }
-    } else if (WALL == 1 && cls == NODE_BOUNDARY) {
+    } else if (WALL == 1 && cls == NODE_BOUNDARY && OWN == OWN_OPP) {
         // Eq. 11 on blocked links: each wall returns its discrete Maxwellian at the wall velocity,
         // f_i = w_i rho_w (1 + e_i(U_w)), with rho_w set so that the node gets back exactly the mass
         // it sends into that wall (per wall: body = bits of .x, static wall = bits of .y)
@@ -440,29 +450,36 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src, v
 
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
 // the slots in a fixed order, adds the constant part and writes the force of the step.
-__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double2* force_out, double Fx, double Fy) {
+template <int NF>
+__device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int tile, double2* force_out, double (&F)[2 * NF]) {
     const int slot = P.tile_slot[tile];
     if (slot < 0) return;  // block-uniform: no body link in this tile
-    __shared__ double2 red[32];
+    __shared__ double2 red[32 * NF];
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nwarps = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        Fx += __shfl_down_sync(0xffffffffu, Fx, o);
-        Fy += __shfl_down_sync(0xffffffffu, Fy, o);
+#pragma unroll
+        for (int c = 0; c < 2 * NF; ++c) F[c] += __shfl_down_sync(0xffffffffu, F[c], o);
     }
-    if ((tid & 31) == 0) red[tid >> 5] = make_double2(Fx, Fy);
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) red[(tid >> 5) * NF + f] = make_double2(F[2 * f], F[2 * f + 1]);
+    }
     __syncthreads();
     if (tid < 32) {
-        double2 v = tid < nwarps ? red[tid] : make_double2(0.0, 0.0);
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        for (int f = 0; f < NF; ++f) {
+            double2 v = tid < nwarps ? red[tid * NF + f] : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+            }
+            if (tid == 0) P.partials[slot * NF + f] = v;
         }
         if (tid == 0) {
-            P.partials[slot] = v;
             __threadfence();
             const unsigned t = atomicAdd(P.ticket, 1u);
             last = (t == (unsigned)(P.nslots - 1));
@@ -471,24 +488,32 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
     __syncthreads();
     if (last && tid < 32) {
         __threadfence();
-        double sx = 0.0, sy = 0.0;
-        for (int k = tid; k < P.nslots; k += 32) {
-            const double2 v = __ldcg(P.partials + k);
-            sx += v.x;
-            sy += v.y;
-        }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            sx += __shfl_down_sync(0xffffffffu, sx, o);
-            sy += __shfl_down_sync(0xffffffffu, sy, o);
+        for (int f = 0; f < NF; ++f) {
+            double sx = 0.0, sy = 0.0;
+            for (int k = tid; k < P.nslots; k += 32) {
+                const double2 v = __ldcg(P.partials + k * NF + f);
+                sx += v.x;
+                sy += v.y;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                sx += __shfl_down_sync(0xffffffffu, sx, o);
+                sy += __shfl_down_sync(0xffffffffu, sy, o);
+            }
+            if (tid == 0) {
+                const double2 Fs = make_double2(sx + P.fconst.x, sy + P.fconst.y);
+                if (!isfinite(Fs.x) || !isfinite(Fs.y)) atomicOr(P.err, 1);
+                force_out[f] = Fs;
+            }
         }
-        if (tid == 0) {
-            const double2 F = make_double2(sx + P.fconst.x, sy + P.fconst.y);
-            if (!isfinite(F.x) || !isfinite(F.y)) atomicOr(P.err, 1);
-            *force_out = F;
-            *P.ticket = 0u;
-        }
+        if (tid == 0) *P.ticket = 0u;
     }
+}
+
+__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double2* force_out, double Fx, double Fy) {
+    double F[2] = {Fx, Fy};
+    tile_epilogue_n<1>(P, tile, force_out, F);
 }
 
 // One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
@@ -592,8 +617,24 @@ cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+// The plain step on 32 x 4 tiles with an occupancy floor: at least MINB blocks of 128 threads per
+// SM, so the compiler keeps the kernel within 65536 / (128 MINB) registers per thread.  The plain
+// kernel waits on its global loads; more resident warps hide more of that latency.
+template <class L, class ST, int COLL, int MINB>
+__global__ void __launch_bounds__(128, MINB) step_kernel_occ(const __grid_constant__ InstDev P) {
+    process_tile<L, ST, COLL, 0>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
+}
+
+template <class L, class ST, int COLL, int MINB>
+cudaError_t launch_step_occ(const InstDev& P, dim3 block, cudaStream_t stream) {
+    step_kernel_occ<L, ST, COLL, MINB><<<P.ntiles, block, 0, stream>>>(P);
+    return cudaGetLastError();
+}
+
 // Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.
 StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall = 0);
+// Plain step with an occupancy floor: variant 1 = 6 blocks of 128 per SM, 2 = 7 (nullptr if not built).
+StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant);
 // Address of batch_kernel<...> for a cooperative launch (nullptr if not built).
 BatchKernelFn find_batch_kernel(int Q, int storage, int coll);
 

@@ -34,6 +34,30 @@ void* find_launcher_q37_half_ds(int storage, int coll) {
     }
 }
 
+// Plain step with an occupancy floor (16-bit storage): variant 1 = 6, 2 = 7 blocks of 128 per SM.
+void* find_occ_launcher_q37_half(int storage, int coll, int variant) {
+    switch ((storage * 2 + coll) * 4 + variant) {
+        case (ST_BF16 * 2 + COLL_BGK) * 4 + 1:
+            return (void*)&launch_step_occ<D2Q37, __nv_bfloat16, COLL_BGK, 6>;
+        case (ST_BF16 * 2 + COLL_BGK) * 4 + 2:
+            return (void*)&launch_step_occ<D2Q37, __nv_bfloat16, COLL_BGK, 7>;
+        case (ST_BF16 * 2 + COLL_REG) * 4 + 1:
+            return (void*)&launch_step_occ<D2Q37, __nv_bfloat16, COLL_REG, 6>;
+        case (ST_BF16 * 2 + COLL_REG) * 4 + 2:
+            return (void*)&launch_step_occ<D2Q37, __nv_bfloat16, COLL_REG, 7>;
+        case (ST_F16 * 2 + COLL_BGK) * 4 + 1:
+            return (void*)&launch_step_occ<D2Q37, __half, COLL_BGK, 6>;
+        case (ST_F16 * 2 + COLL_BGK) * 4 + 2:
+            return (void*)&launch_step_occ<D2Q37, __half, COLL_BGK, 7>;
+        case (ST_F16 * 2 + COLL_REG) * 4 + 1:
+            return (void*)&launch_step_occ<D2Q37, __half, COLL_REG, 6>;
+        case (ST_F16 * 2 + COLL_REG) * 4 + 2:
+            return (void*)&launch_step_occ<D2Q37, __half, COLL_REG, 7>;
+        default:
+            return nullptr;
+    }
+}
+
 // Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10, 11, 12 = one
 // node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 20, 21, 22 = two nodes per thread on 64 x 4,
 // 64 x 2, 128 x 2 tiles.

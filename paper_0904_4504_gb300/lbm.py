@@ -31,6 +31,7 @@ LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = 0, 1, 2, 3
 LBM_FLUID, LBM_BODY, LBM_WALL = 0, 1, 2
 LBM_BATCH_STREAMS, LBM_BATCH_PERSISTENT = 0, 1
 LBM_SCHEME_BOUNCEBACK, LBM_SCHEME_DIFFUSE = 0, 1
+LBM_LAYOUT_AB, LBM_LAYOUT_AA = 0, 1
 STORAGE_BYTES = {LBM_STORE_F64: 8, LBM_STORE_F32: 4, LBM_STORE_BF16: 2, LBM_STORE_F16: 2}
 
 
@@ -53,6 +54,7 @@ class lbm_geometry(ctypes.Structure):
         ("collision", ctypes.c_int),
         ("storage", ctypes.c_int),
         ("wall_scheme", ctypes.c_int),
+        ("layout", ctypes.c_int),
     ]
 
 
@@ -68,6 +70,7 @@ class lbm_info_t(ctypes.Structure):
         ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
         ("h2d_bytes", ctypes.c_size_t), ("d2h_bytes", ctypes.c_size_t),
         ("variant", ctypes.c_int),
+        ("layout", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -248,9 +251,10 @@ def lbm_params_from_tau_omega(lattice: int, tau_omega: float, delta_min: float =
 
 
 def make_geometry(kind=LBM_GEOM_NONE, lx=0, ly=0, drive=LBM_DRIVE_WALL, u0=0.0, rho0=1.0, mask=None, eq_order=2,
-                  collision=LBM_COLL_REGULARIZED, storage=LBM_STORE_F32, wall_scheme=LBM_SCHEME_BOUNCEBACK):
+                  collision=LBM_COLL_REGULARIZED, storage=LBM_STORE_F32, wall_scheme=LBM_SCHEME_BOUNCEBACK,
+                  layout=LBM_LAYOUT_AB):
     """An lbm_geometry; `mask` (ny x nx uint8) is kept alive on the returned object."""
-    g = lbm_geometry(kind, lx, ly, drive, u0, rho0, None, eq_order, collision, storage, wall_scheme)
+    g = lbm_geometry(kind, lx, ly, drive, u0, rho0, None, eq_order, collision, storage, wall_scheme, layout)
     if mask is not None:
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         g._mask_ref = m

@@ -83,6 +83,21 @@ def test_batch_footprint_counts_both_population_buffers():
     assert 2 * 37 * 1024 * 1024 * 4 < n < 2 * 37 * 1024 * 1024 * 4 + 40 * 1024 * 1024
 
 
+def test_batch_footprint_of_the_in_place_layout_holds_one_buffer():
+    kw = dict(kind=L.LBM_GEOM_BEAM, lx=32, ly=32, storage=L.LBM_STORE_F16)
+    ab = L.lbm_batch_footprint(L.make_instance(37, 2048, 2048, 0.9, 0.05, 3840, **kw))
+    aa = L.lbm_batch_footprint(L.make_instance(37, 2048, 2048, 0.9, 0.05, 3840, layout=L.LBM_LAYOUT_AA, **kw))
+    assert ab - aa == 37 * 2048 * 2048 * 2
+
+
+def test_create_rejects_bad_layout_and_diffuse_in_place():
+    for kw in (dict(layout=7), dict(layout=L.LBM_LAYOUT_AA, wall_scheme=L.LBM_SCHEME_DIFFUSE)):
+        geom = L.make_geometry(kind=L.LBM_GEOM_NONE, u0=1e-3, **kw)
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_create(37, 64, 64, 0.8, 0.1, geom)
+        assert e.value.code == L.LBM_EINVAL
+
+
 def test_batch_create_rejects_bad_arguments():
     with pytest.raises(L.LbmError) as e:
         L.lbm_batch_create(11, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)

@@ -46,10 +46,10 @@ ROUND16 = {L.LBM_STORE_BF16: 2.0 ** -8, L.LBM_STORE_F16: 2.0 ** -11}
 
 def run_both(Q, nx, ny, tau, omega, kind, steps, *, lx=0, ly=0, mask=None, drive=L.LBM_DRIVE_WALL, u0=1e-3,
              eq_order=2, collision=L.LBM_COLL_REGULARIZED, storage=L.LBM_STORE_F64, init_exp=None, seed=0,
-             tile=None, n0_chunks=1, wall=L.LBM_SCHEME_BOUNCEBACK):
+             tile=None, n0_chunks=1, wall=L.LBM_SCHEME_BOUNCEBACK, layout=L.LBM_LAYOUT_AB):
     """Run `steps` steps on the GPU and on the oracle; returns (g_gpu, g_or, F_gpu, F_or, labels, g0)."""
     geom = L.make_geometry(kind=kind, lx=lx, ly=ly, drive=drive, u0=u0, mask=mask, eq_order=eq_order,
-                           collision=collision, storage=storage, wall_scheme=wall)
+                           collision=collision, storage=storage, wall_scheme=wall, layout=layout)
     lab_or = oracle_labels(kind, Q, nx, ny, lx, ly, mask)
     s = 1.0 if L.STORAGE_BYTES[storage] > 2 else u0
     _, w, _ = L.lbm_lattice_velocities(Q)
@@ -134,6 +134,13 @@ CASES = [
      L.LBM_COLL_REGULARIZED, L.LBM_STORE_F32, 30, -17, None),
     ("q37-bgk-h4-mask-wall-f32", 37, 67, 53, L.LBM_GEOM_MASK, 0, 0, L.LBM_DRIVE_WALL, 4, L.LBM_COLL_BGK,
      L.LBM_STORE_F32, 25, -17, (64, 4)),
+    # lab frame: the beam's walls move (Sec. 6), no body force
+    ("q9-reg-beam-lab-f64", 9, 45, 37, L.LBM_GEOM_BEAM, 9, 7, L.LBM_DRIVE_WALL, 2, L.LBM_COLL_REGULARIZED,
+     L.LBM_STORE_F64, 40, -17, None),
+    ("q37-reg-h4-beam-lab-f64", 37, 70, 41, L.LBM_GEOM_BEAM, 12, 9, L.LBM_DRIVE_WALL, 4,
+     L.LBM_COLL_REGULARIZED, L.LBM_STORE_F64, 30, -17, (32, 4)),
+    ("q37-reg-h4-beam-lab-f32", 37, 70, 41, L.LBM_GEOM_BEAM, 12, 9, L.LBM_DRIVE_WALL, 4,
+     L.LBM_COLL_REGULARIZED, L.LBM_STORE_F32, 30, -17, (64, 2)),
 ]
 
 
@@ -161,6 +168,18 @@ def test_parity_16bit_one_step(st, coll):
     assert_force_close(F_gpu, F_or, Q, lab, st, 1)
 
 
+@pytest.mark.parametrize("st", [L.LBM_STORE_BF16, L.LBM_STORE_F16])
+def test_parity_16bit_one_step_lab_frame(st):
+    """Moving-wall beam in 16-bit storage: no stream offset (the far fluid is at rest), so each
+    output is the exact step rounded once, relative to its own magnitude."""
+    Q, nx, ny = 37, 70, 41
+    g_gpu, g_or, F_gpu, F_or, lab, g0 = run_both(Q, nx, ny, 0.9, 0.05, L.LBM_GEOM_BEAM, 1, lx=12, ly=9,
+                                                 drive=L.LBM_DRIVE_WALL, u0=2e-3, eq_order=4, storage=st,
+                                                 init_exp=-7, seed=6)
+    assert_state_close(Q, g_gpu, g_or, lab, st, 1, g0)
+    assert_force_close(F_gpu, F_or, Q, lab, st, 1)
+
+
 def test_parity_plate_d2q9_fp64_full_config():
     """The D2Q9 plate workload itself (4 x 256, tau = 0.8, omega = 1/3, U0 = 1e-3, 20 periods) from rest."""
     w = I.plate_d2q9_fp64()
@@ -185,7 +204,8 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
     Q, nx, ny = 37, 200, 90
     outs = []
     configs = [("tile", (32, 8)), ("tile", (64, 4)), ("tile", (128, 1)), ("tile", (32, 16)),
-               ("variant", 10), ("variant", 11), ("variant", 12), ("variant", 20), ("variant", 21), ("variant", 22)]
+               ("variant", 1), ("variant", 2), ("variant", 10), ("variant", 11), ("variant", 12), ("variant", 20),
+               ("variant", 21), ("variant", 22)]
     for kind, arg in configs:
         geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
                                storage=storage)
@@ -211,9 +231,10 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
         assert np.abs(F - outs[0][1]).max() <= Ftol, (kind, arg)
 
 
-@pytest.mark.parametrize("variant", [10, 11, 12, 20, 21, 22])
+@pytest.mark.parametrize("variant", [1, 2, 10, 11, 12, 20, 21, 22])
 def test_parity_staged_variants(variant):
-    """The TMA-staged kernels against the oracle on a grid with interior tiles, FP32."""
+    """The occupancy-floor (1, 2) and TMA-staged kernels against the oracle on a grid with interior
+    tiles, FP32."""
     Q, nx, ny, steps = 37, 200, 90, 12
     geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=2e-3, eq_order=4,
                            storage=L.LBM_STORE_F32)
