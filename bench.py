@@ -126,9 +126,8 @@ class ClockSampler:
 
 def dist_setup(n_gpus):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_0904_4504_gb300.replicas import env_rank
+    rank, world, local = env_rank()
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -139,25 +138,22 @@ def dist_setup(n_gpus):
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_0904_4504_gb300.replicas import barrier as b
+    b(world)
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_0904_4504_gb300.replicas import max_over_ranks as m
+    return m(x, world, device="cuda")
 
 
-def create(L, w, orc_params):
+LAYOUT = {"ab": 0, "aa": 1}
+
+
+def create(L, w, orc_params, layout="ab"):
     tau, omega = orc_params(w)
     geom = L.make_geometry(kind=w.geometry, lx=w.lx, ly=w.ly, drive=w.drive, u0=w.u0, eq_order=w.eq_order,
-                           collision=w.collision, storage=w.storage)
+                           collision=w.collision, storage=w.storage, layout=LAYOUT[layout])
     return L.lbm_create(w.lattice, w.nx, w.ny, tau, omega, geom)
 
 
@@ -170,14 +166,14 @@ def lattice_params(L):
     return f
 
 
-def sweep_descs(L, storage):
+def sweep_descs(L, storage, layout="ab"):
     from paper_0904_4504_gb300 import inputs as I
     out = []
     for w in I.sweep_d2q37():
         tau, omega, P = L.lbm_params_from_tau_omega(37, w.tau_omega)
         out.append((w, L.make_instance(37, w.nx, w.ny, tau, omega, int(w.periods * P), kind=w.geometry, lx=w.lx,
                                        ly=w.ly, drive=w.drive, u0=w.u0, eq_order=w.eq_order, collision=w.collision,
-                                       storage=storage)))
+                                       storage=storage, layout=LAYOUT[layout])))
     return out
 
 
@@ -186,11 +182,11 @@ def run_batch(args, sub=False):
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
 
-    rank, world, local = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-                          int(os.environ.get("LOCAL_RANK", "0"))) if sub else dist_setup(args.gpus)
+    from paper_0904_4504_gb300.replicas import env_rank
+    rank, world, local = env_rank() if sub else dist_setup(args.gpus)
     build()
     storage = STORE[args.workload.split("-")[1]] if "-" in args.workload else STORE["f32"]
-    descs = sweep_descs(L, storage)[:args.instances or None]
+    descs = sweep_descs(L, storage, args.layout)[:args.instances or None]
     stream = torch.cuda.Stream()
     b = L.lbm_batch_create(37, storage, 1)
     L.lbm_batch_set_mode(b, args.batch_mode)
@@ -262,7 +258,7 @@ def run_batch(args, sub=False):
                        "collision": "regularized", "fluid_nodes": fluid, "steps_per_launch": args.chunk,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
-                       "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"]},
+                       "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
@@ -285,11 +281,12 @@ def run_serve(args, sub=False):
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
 
-    rank, world, local = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-                          int(os.environ.get("LOCAL_RANK", "0"))) if sub else dist_setup(args.gpus)
+    from paper_0904_4504_gb300.replicas import env_rank
+    rank, world, local = env_rank() if sub else dist_setup(args.gpus)
     build()
     storage = STORE["f16"] if args.workload.endswith("-f16") else STORE["f32"]
-    stream = I.serving_requests()[rank * args.requests:(rank + 1) * args.requests]
+    from paper_0904_4504_gb300.replicas import rank_slice
+    stream = rank_slice(I.serving_requests(), rank, args.requests)
     reqs, gpu_s = [], []
     peak, peak_kind = peaks()
     for r in stream:
@@ -297,7 +294,8 @@ def run_serve(args, sub=False):
         tau, omega, P = L.lbm_params_from_tau_omega(w.lattice, w.tau_omega)
         nsteps = int(round(w.periods * P))
         d = L.make_instance(w.lattice, w.nx, w.ny, tau, omega, nsteps, kind=w.geometry, lx=w.lx, ly=w.ly,
-                            drive=w.drive, u0=w.u0, eq_order=w.eq_order, collision=w.collision, storage=storage)
+                            drive=w.drive, u0=w.u0, eq_order=w.eq_order, collision=w.collision, storage=storage,
+                            layout=LAYOUT[args.layout])
         perim = 2.0 * (w.lx + w.ly) if w.geometry == 1 else float(w.nx)
         reqs.append((r.arrival_s, L.make_request(d, w.periods / 2.0, perim)))
         bytes_lu = 2 * w.lattice * L.STORAGE_BYTES[storage]
@@ -340,7 +338,7 @@ def run_serve(args, sub=False):
             "scaling": "weak", "vs_baseline": None, "dtype": {v: k for k, v in STORE.items()}[storage],
             "data": "synthetic",
             "config": {"workload": args.workload, "requests": len(reqs), "offered_load": args.load or "as generated",
-                       "steps_per_round": args.chunk, "parallelism": f"replicas x{world}"},
+                       "steps_per_round": args.chunk, "parallelism": f"replicas x{world}", "layout": args.layout},
             "latency": {"p50_s": round(float(np.percentile(lat, 50)), 4),
                         "p99_s": round(float(np.percentile(lat, 99)), 4), "mean_s": round(float(lat.mean()), 4),
                         "max_s": round(float(lat.max()), 4)},
@@ -422,7 +420,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     sims = []
     for w in wl:
-        h = create(L, w, params)
+        h = create(L, w, params, args.layout)
         L.lbm_set_stream(h, stream)
         if args.tile:
             L.lbm_set_tile(h, *args.tile)
@@ -467,7 +465,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         h2d = d2h = 0
         for w in wl:
-            h = create(L, w, params)
+            h = create(L, w, params, args.layout)
             L.lbm_step(h, args.steps)
             F = L.lbm_force_history(h)
             d2h += F.nbytes
@@ -496,14 +494,14 @@ def run_ours(args):
         sl = run_serve(a, sub=True)
         if rank == 0:
             extras["batched_mixed_precision"] = {
-                "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024) in one "
-                            "persistent cooperative launch per 64 steps, FP16 storage scaled by U0, FP32 arithmetic, "
-                            "FP64 force",
+                "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024), "
+                            "streams mode (one launch of the staged step kernel per instance per step, on 8 "
+                            "parallel streams), FP16 storage scaled by U0, FP32 arithmetic, FP64 force",
                 "value": bl["value"], "unit": "MLUPS", "steps": bl["steps"], "ms_per_step": bl["ms_per_step"],
                 "roofline": bl["roofline"], "clocks": bl["clocks"], "gpu_launches": bl["gpu_launches"],
                 "speedup_vs_plain_fp32": round(bl["value"] / value, 4),
-                "force_error_vs_oracle": "FP16 storage <= 6e-5 of the force amplitude (in-phase and quadrature, "
-                                         "tests/test_gpu_precision.py); target 1e-4"}
+                "force_error_vs_oracle": "FP16 storage <= 1.6e-5 of the force amplitude (in-phase and quadrature, "
+                                         "body and lab frame, tests/test_gpu_precision.py); target 1e-4"}
             extras["serving"] = {k: sl[k] for k in ("value", "unit", "config", "latency", "server", "clocks")}
     if rank == 0:
         w0 = wl[0]
@@ -517,11 +515,12 @@ def run_ours(args):
                        "nodes_per_instance": [w.nx * w.ny for w in wl], "fluid_nodes": fluid,
                        "l2": "inputs larger than L2 (no flush)" if bytes_step / len(wl) > 2 * 129e6 else
                              "inputs smaller than L2", "parallelism": f"replicas x{world}",
-                       "tile": [infos[0]["block_x"], infos[0]["block_y"]], "variant": infos[0]["variant"]},
+                       "tile": [infos[0]["block_x"], infos[0]["block_y"]], "variant": infos[0]["variant"],
+                       "layout": args.layout},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": args.traffic if args.traffic is not None else
-                         TRAFFIC.get((args.workload, infos[0]["variant"])),
+                         TRAFFIC.get((args.workload, infos[0]["variant"])) if args.layout == "ab" else None,
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": "step_kernel (fused stream+collide+force)",
                          "bytes_per_launch": bytes_step // len(wl)},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
@@ -616,6 +615,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, nargs=2, default=None)
     ap.add_argument("--variant", type=int, default=None, help="step kernel variant (lbm_set_variant)")
+    ap.add_argument("--layout", default="ab", choices=["ab", "aa"],
+                    help="population layout: two buffers (ab) or one buffer updated in place (aa)")
     ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64, serve)")
     ap.add_argument("--requests", type=int, default=24, help="requests per rank (serve)")
     ap.add_argument("--load", type=float, default=0.7, help="offered load, fraction of capacity (serve; 0: as generated)")

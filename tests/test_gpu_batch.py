@@ -191,3 +191,23 @@ def test_batch_sweep_shapes_run(mode):
         assert info["live"] == 64 and info["running"] == 64 and info["mode"] == mode
     finally:
         L.lbm_batch_destroy(b)
+
+
+def test_damping_sweep_matches_direct_fit():
+    """The Q(p) sweep driver gives the gamma_bar of a direct run of the same instance."""
+    from paper_0904_4504_gb300 import resonators as R
+    rec = R.damping_sweep([1.0], 1.0, side=128, periods=4, lx_max=16, ly_max=16)[0]
+    P = rec["period"]
+    tau, omega, P = L.lbm_params_from_tau_omega(37, 1.0, p_min=P)
+    assert (tau, omega) == (rec["tau"], rec["omega"]) and rec["u0"] == 1e-3
+    geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=16, ly=16, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
+                           storage=L.LBM_STORE_F32)
+    h = L.lbm_create(37, 128, 128, tau, omega, geom)
+    try:
+        L.lbm_set_tile(h, 32, 4)
+        L.lbm_step(h, 4 * P)
+        f_in, _, _ = L.lbm_fit(h, 2.0)
+        direct = L.lbm_gamma_bar(h, f_in, 64.0)
+    finally:
+        L.lbm_destroy(h)
+    assert rec["gamma_bar"] == direct and direct > 0

@@ -53,9 +53,10 @@ def test_free_molecular_scaling():
     assert abs(gf[1] / gf[0] - 3.0) < 1e-12
 
 
-def test_interpolation_is_log_linear_and_saturates():
+def test_interpolation_is_log_linear_saturates_and_continues_as_sqrt():
     f = R.interpolated([0.01, 1.0, 100.0], [0.1, 1.0, 2.0])
-    assert abs(f(0.1) - 0.55) < 1e-12 and abs(f(1e6) - 2.0) < 1e-12 and abs(f(1e-6) - 0.1) < 1e-12
+    assert abs(f(0.1) - 0.55) < 1e-12 and abs(f(1e6) - 2.0) < 1e-12
+    assert abs(f(1e-6) - 0.1 * math.sqrt(1e-4)) < 1e-15
 
 
 def test_beam_sections_have_the_table_aspect_ratios():
@@ -67,9 +68,24 @@ def test_beam_sections_have_the_table_aspect_ratios():
 
 def test_quality_curves_vacuum_to_atmosphere(monkeypatch):
     """With a saturating damping curve, Q/Q_o -> 1 at low pressure and falls with p for every device."""
-    monkeypatch.setattr(R, "damping_sweep", lambda tos, ar, **kw: [0.9 * t / (1 + t) + 0.1 * math.sqrt(t)
+    monkeypatch.setattr(R, "damping_sweep", lambda tos, ar, **kw: [{"gamma_bar": 0.9 * t / (1 + t) + 0.1 * math.sqrt(t)}
                                                                    for t in tos])
     res = R.quality_curves(pressures_torr=[1e-4, 1.0, 1e3])
     for d in res["devices"]:
         q = d["q_over_q0"]
         assert q[0] > 0.99 and q[0] > q[1] > q[2] > 0
+
+
+def test_sweep_period_balances_compactness_and_mean_free_path():
+    th = 1 / 1.19697977039307 ** 2
+    c_s = math.sqrt(th)
+    # small tau*omega: the acoustic period (omega L / c_s = 1/4) wins
+    P = R.sweep_period(1e-3, 208, 1024, th, 128)
+    assert abs(2 * math.pi / P * 208 / c_s - 0.25) < 1e-3
+    # large tau*omega: capped so that c_s tau <= box / 4, never below the resolution rule
+    P = R.sweep_period(1.0, 208, 1024, th, 128)
+    tau = 1.0 * P / (2 * math.pi)
+    assert c_s * tau <= 1024 / 4 + c_s and P > 128
+    assert R.sweep_period(100.0, 208, 1024, th, 128) == 128
+    # the plate has no length: resolution and mean free path only
+    assert R.sweep_period(1e-3, 0, 4096, th, 673) == 673
