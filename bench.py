@@ -190,6 +190,8 @@ def run_batch(args, sub=False):
     stream = torch.cuda.Stream()
     b = L.lbm_batch_create(37, storage, 1)
     L.lbm_batch_set_mode(b, args.batch_mode)
+    if args.batch_variant is not None:
+        L.lbm_batch_set_variant(b, args.batch_variant)
     L.lbm_batch_set_stream(b, stream)
     for _, d in descs:
         L.lbm_batch_add(b, d)
@@ -234,6 +236,8 @@ def run_batch(args, sub=False):
         t0 = time.perf_counter()
         b = L.lbm_batch_create(37, storage, 1)
         L.lbm_batch_set_mode(b, args.batch_mode)
+        if args.batch_variant is not None:
+            L.lbm_batch_set_variant(b, args.batch_variant)
         slots = [L.lbm_batch_add(b, d) for _, d in descs]
         run(args.steps)
         L.lbm_batch_synchronize(b)
@@ -258,7 +262,8 @@ def run_batch(args, sub=False):
                        "collision": "regularized", "fluid_nodes": fluid, "steps_per_launch": args.chunk,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
-                       "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout},
+                       "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout,
+                       "kernel_variant": "default" if args.batch_variant is None else args.batch_variant},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
@@ -624,6 +629,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="beam1024: skip the batched and serving parts")
     ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
     ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
+    ap.add_argument("--batch-variant", type=int, default=None, help="sweep64: step kernel of the streams mode")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

@@ -179,9 +179,10 @@ int lbm_info(lbm_sim* sim, lbm_info_t* out);
 int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
 
 /* Choose the step kernel.  0: plain kernel, one block per tile of lbm_set_tile's shape, wrapped
- * global loads (the default).  1, 2: the plain kernel on 32 x 4 tiles compiled for at least 6 (1)
- * or 7 (2) resident blocks per SM (fewer registers, more warps to hide load latency; D2Q37,
- * FP32/BF16/FP16 storage).  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
+ * global loads.  1, 2: the plain kernel on 32 x 4 tiles compiled for at least 6 (1) or 7 (2)
+ * resident blocks per SM (fewer registers, more warps to hide load latency; D2Q37, FP32/BF16/FP16
+ * storage).  lbm_create starts D2Q37 two-buffer bounce-back runs on variant 1 (FP32) or 2
+ * (16-bit), the fastest single-instance kernels measured; lbm_set_tile selects variant 0.  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
  * copied to shared memory by bulk tensor copies (TMA), one box per direction plane:
  * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
  * 20, 21, 22: two neighbouring nodes per thread (paired loads and stores), tiles of 64 x 4,
@@ -294,6 +295,13 @@ int lbm_batch_remove(lbm_batch* batch, int slot);
 
 /* Choose the mode (before the first lbm_batch_add). */
 int lbm_batch_set_mode(lbm_batch* batch, int mode);
+
+/* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
+ * numbers; -1, the default: the staged variant 11 for 16-bit storage, variant 2 for D2Q37 FP32,
+ * else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
+ * support falls back to the plain kernel.  Ignored by the persistent mode.  LBM_EINVAL for a number
+ * below -1. */
+int lbm_batch_set_variant(lbm_batch* batch, int variant);
 
 /* Clock cycles a block waits at a grid barrier before giving up (test hook: 0 gives up at once). */
 int lbm_batch_set_barrier_limit(lbm_batch* batch, long long cycles);

@@ -39,6 +39,7 @@ constexpr int kSubStreams = 8;
 struct lbm_batch {
     int device = 0, Q = 0, storage = 0, collision = 0;
     int mode = LBM_BATCH_STREAMS;
+    int variant = -1;                     // kernel of instances added in the streams mode (-1: default)
     cudaStream_t sub[kSubStreams] = {};   // instance launches (streams mode), one chain per instance
     cudaEvent_t ev_fork = nullptr, ev_join[kSubStreams] = {};
     int bx = 32, by = 4;
@@ -315,8 +316,12 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     // kernel shape, history and stream, on the instance's own stream first, so that adding an
     // instance does not wait for a run of the batch that may be in flight
     if (b->mode == LBM_BATCH_PERSISTENT) sim_disable_stream_offset(sim);  // the kernel reads fixed params
-    if (b->mode == LBM_BATCH_PERSISTENT || b->storage == LBM_STORE_F32 || b->storage == LBM_STORE_F64 ||
-        lbm_set_variant(sim, 11) != LBM_OK)
+    // default kernels, fastest measured in this mode: staged (11) for 16-bit storage, the plain
+    // kernel with 7 resident blocks per SM (2) for D2Q37 FP32, else the plain kernel
+    const int want = b->variant >= 0 ? b->variant
+                     : (b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16) ? 11
+                     : (b->Q == 37 && b->storage == LBM_STORE_F32) ? 2 : 0;
+    if (b->mode == LBM_BATCH_PERSISTENT || want == 0 || lbm_set_variant(sim, want) != LBM_OK)
         rc = lbm_set_tile(sim, b->bx, b->by);
     if (rc) return undo(rc);
     clear_error();
@@ -512,6 +517,14 @@ int lbm_batch_set_mode(lbm_batch* b, int mode) {
     for (const Slot& s : b->slots)
         if (slot_live(s)) return set_error(LBM_EINVAL, "set the mode before adding instances");
     b->mode = mode;
+    return LBM_OK;
+}
+
+int lbm_batch_set_variant(lbm_batch* b, int variant) {
+    int rc = check_batch(b);
+    if (rc) return rc;
+    if (variant < -1) return set_error(LBM_EINVAL, "bad variant %d", variant);
+    b->variant = variant;
     return LBM_OK;
 }
 

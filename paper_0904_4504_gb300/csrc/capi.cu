@@ -735,6 +735,16 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.reg_a_f = (float)d.reg_a;
     d.src_k_f = (float)d.src_k;
     s->stream_off = es == 2 && g.drive == LBM_DRIVE_BODYFORCE;
+    // default kernel on the default 32 x 4 tile: the fastest measured single-instance form, the
+    // plain kernel with an occupancy floor (variant 1 for FP32, 2 for 16-bit storage)
+    if (!s->aa && g.wall_scheme == LBM_SCHEME_BOUNCEBACK) {
+        const int v = es == 4 ? 1 : es == 2 ? 2 : 0;
+        StepLaunchFn f = v ? find_occ_launcher(lattice, g.storage, g.collision, v) : nullptr;
+        if (f) {
+            s->launch = f;
+            s->variant = v;
+        }
+    }
     TRY_OR_FREE(setup_tiles(s));
     TRY_OR_FREE(ensure_capacity(s, 1024));
     *out = s;

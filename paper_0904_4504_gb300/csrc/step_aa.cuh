@@ -26,14 +26,12 @@
 
 namespace lbm {
 
-// h_i = A[x - c_i][opp(i)], periodic in x and y.
-template <class L, class ST>
-__device__ __forceinline__ void gather_swapped(const InstDev& P, const ST* src, int x, int y,
-                                               typename StoreT<ST>::CT (&h)[L::Q]) {
-    using S = StoreT<ST>;
-    constexpr int Q = L::Q, R = L::R;
-    const long long plane = P.plane;
-    int roff[2 * R + 1], col[2 * R + 1];
+// Rows and columns y - d, x - d (d = -R..R, periodic) around node (x, y): the pull source x - c_i
+// of direction i is (roff[cy + R], col[cx + R]) and its push target x + c_i is (roff[R - cy],
+// col[R - cx]), so one table serves both.
+template <int R>
+__device__ __forceinline__ void neighbour_table(const InstDev& P, int x, int y, int (&roff)[2 * R + 1],
+                                                int (&col)[2 * R + 1]) {
 #pragma unroll
     for (int d = -R; d <= R; ++d) {
         int ys = y - d;
@@ -45,51 +43,28 @@ __device__ __forceinline__ void gather_swapped(const InstDev& P, const ST* src, 
         roff[d + R] = ys * P.pitch;
         col[d + R] = xs;
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-        h[i] = S::ld(src + opp_of<L>(i) * plane + roff[cy + R] + col[cx + R]);
-    }
 }
 
-// Even step of one node: pull (swapped), wall fix-up, collide, push.  (Fx, Fy) gets the force of
-// step n, (Gx, Gy) the force of step n + 1 from the links bounced on the push.
-template <class L, class ST, int COLL>
-__device__ __forceinline__ void aa_pull_push(const InstDev& P, ST* A, int x, int y, int cls, double& Fx,
-                                             double& Fy, double& Gx, double& Gy) {
+// Collision outputs of one node pushed to their targets.  BND: the node has blocked links, and an
+// output whose link x -> x + c_i is blocked (exactly when pull link opp(i) is) comes back into the
+// node's own slot A[x][opp(i)] with the wall term of step n + 1; its momentum exchange goes to
+// (Gx, Gy), the force of step n + 1.  Bulk nodes push every output without tests.
+template <class L, class ST, int COLL, bool BND>
+__device__ __forceinline__ void aa_push(const InstDev& P, ST* A, int idx, const int (&roff)[2 * L::R + 1],
+                                        const int (&col)[2 * L::R + 1], const Coef<typename StoreT<ST>::CT>& C,
+                                        const typename StoreT<ST>::CT (&h)[L::Q], double& Gx, double& Gy) {
     using S = StoreT<ST>;
     using T = typename S::CT;
-    constexpr int Q = L::Q, R = L::R;
+    constexpr int R = L::R;
     const long long plane = P.plane;
-    const int idx = y * P.pitch + x;
-    T h[Q];
-    gather_swapped<L, ST>(P, A, x, y, h);
-    Coef<T> C;
-    prepare<L, ST, COLL, 0, OWN_SWAPPED>(P, A, x, y, cls, P.dv, P.dv_f, h, Fx, Fy, C);
-
-    // push targets: rows and columns of x + c_i, periodic
-    int roff[2 * R + 1], col[2 * R + 1];
-#pragma unroll
-    for (int d = -R; d <= R; ++d) {
-        int ys = y + d;
-        ys += ys < 0 ? P.ny : 0;
-        ys -= ys >= P.ny ? P.ny : 0;
-        int xs = x + d;
-        xs += xs < 0 ? P.nx : 0;
-        xs -= xs >= P.nx ? P.nx : 0;
-        roff[d + R] = ys * P.pitch;
-        col[d + R] = xs;
-    }
-    // link x -> x + c_i is blocked exactly when pull link opp(i) of x is
-    ulonglong2 lk = make_ulonglong2(0ull, 0ull);
-    if (cls == NODE_BOUNDARY) lk = P.links[idx];
-    const unsigned long long blk = lk.x | lk.y;
     const bool off = sizeof(ST) == 2 && P.stream_off;
+    ulonglong2 lk = make_ulonglong2(0ull, 0ull);
+    if (BND) lk = P.links[idx];
+    const unsigned long long blk = lk.x | lk.y;
 
     auto push = [&](int i, T o) {
         const int j = opp_of<L>(i);
-        if ((blk >> j) & 1ull) {
-            // comes back as direction j at x in step n + 1 (Eq. 12 with U_w of step n + 1)
+        if (BND && ((blk >> j) & 1ull)) {
             double mw = 0.0;
             if ((lk.x >> j) & 1ull) {
                 if (P.moving) mw = P.mw_k * cx_of<L>(j) * P.dv2;
@@ -102,7 +77,7 @@ __device__ __forceinline__ void aa_pull_push(const InstDev& P, ST* A, int x, int
             }
             S::st(A + j * plane + idx, o + (T)mw - (off ? (T)P.Hs[j] : (T)0));
         } else {
-            S::st(A + i * plane + roff[cy_of<L>(i) + R] + col[cx_of<L>(i) + R], o - (off ? (T)P.Hs[i] : (T)0));
+            S::st(A + i * plane + roff[R - cy_of<L>(i)] + col[R - cx_of<L>(i)], o - (off ? (T)P.Hs[i] : (T)0));
         }
     };
     S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)P.Hs[0] : (T)0));
@@ -113,6 +88,36 @@ __device__ __forceinline__ void aa_pull_push(const InstDev& P, ST* A, int x, int
         push(1 + 2 * k, op);
         push(2 + 2 * k, omn);
     }
+}
+
+// Even step of one node: pull h_i = A[x - c_i][opp(i)], wall fix-up from the node's own plane i,
+// collide, push.  (Fx, Fy) gets the force of step n, (Gx, Gy) that of step n + 1.  The neighbour
+// table is built twice, for the pull and again for the push, rather than kept live through the
+// collision (registers).
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void aa_pull_push(const InstDev& P, ST* A, int x, int y, int cls, double& Fx,
+                                             double& Fy, double& Gx, double& Gy) {
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    constexpr int Q = L::Q, R = L::R;
+    const long long plane = P.plane;
+    const int idx = y * P.pitch + x;
+    T h[Q];
+    {
+        int roff[2 * R + 1], col[2 * R + 1];
+        neighbour_table<R>(P, x, y, roff, col);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            h[i] = S::ld(A + opp_of<L>(i) * plane + roff[cy_of<L>(i) + R] + col[cx_of<L>(i) + R]);
+    }
+    Coef<T> C;
+    prepare<L, ST, COLL, 0, OWN_SWAPPED>(P, A, x, y, cls, P.dv, P.dv_f, h, Fx, Fy, C);
+    int roff[2 * R + 1], col[2 * R + 1];
+    neighbour_table<R>(P, x, y, roff, col);
+    if (cls == NODE_BOUNDARY)
+        aa_push<L, ST, COLL, true>(P, A, idx, roff, col, C, h, Gx, Gy);
+    else
+        aa_push<L, ST, COLL, false>(P, A, idx, roff, col, C, h, Gx, Gy);
 }
 
 // Odd step of one node: local read, collide, store directions swapped.

@@ -193,6 +193,7 @@ def lib():
             "lbm_batch_remove": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_set_barrier_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
             "lbm_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_batch_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
             "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
             "lbm_batch_destroy": (None, [_P]),
@@ -421,6 +422,10 @@ def lbm_batch_remove(batch: int, slot: int) -> None:
 
 def lbm_batch_set_mode(batch: int, mode: int) -> None:
     _check(lib().lbm_batch_set_mode(batch, mode))
+
+
+def lbm_batch_set_variant(batch: int, variant: int) -> None:
+    _check(lib().lbm_batch_set_variant(batch, variant))
 
 
 def lbm_batch_set_barrier_limit(batch: int, cycles: int) -> None:

@@ -30,13 +30,27 @@ def _desc(Q, nx, ny, tau, omega, nsteps, storage=L.LBM_STORE_F32, coll=L.LBM_COL
     return L.make_instance(Q, nx, ny, tau, omega, nsteps, **geo)
 
 
-def _alone(d):
-    """Run an instance description through the single-instance path, with the batch's tile shape
-    (the tile shape fixes the order in which the FP64 force partials are summed)."""
+def batch_kernel_variant(d, mode=L.LBM_BATCH_STREAMS):
+    """The kernel a batch runs an instance with by default (lbm_batch_set_variant)."""
+    g = d.geom
+    if mode != L.LBM_BATCH_STREAMS or g.layout != L.LBM_LAYOUT_AB or g.wall_scheme != L.LBM_SCHEME_BOUNCEBACK:
+        return 0
+    if g.storage in (L.LBM_STORE_BF16, L.LBM_STORE_F16):
+        return 11
+    return 2 if (d.lattice == 37 and g.storage == L.LBM_STORE_F32) else 0
+
+
+def _alone(d, mode=L.LBM_BATCH_STREAMS):
+    """Run an instance description through the single-instance path, with the batch's kernel and
+    tile shape (the tile shape fixes the order in which the FP64 force partials are summed)."""
     g = d.geom
     h = L.lbm_create(d.lattice, d.nx, d.ny, d.tau, d.omega, g)
     try:
-        L.lbm_set_tile(h, 32, 4)
+        v = batch_kernel_variant(d, mode)
+        if v:
+            L.lbm_set_variant(h, v)
+        else:
+            L.lbm_set_tile(h, 32, 4)
         L.lbm_step(h, d.nsteps)
         return L.lbm_get_state(h), L.lbm_force_history(h)
     finally:
@@ -73,7 +87,7 @@ def test_batch_equals_standalone_bitwise(mode):
             assert done == total == d.nsteps
             sim = L.lbm_batch_instance(b, s)
             g_b, F_b = L.lbm_get_state(sim), L.lbm_force_history(sim)
-            g_a, F_a = _alone(d)
+            g_a, F_a = _alone(d, mode)
             assert (g_b == g_a).all(), d.nx
             assert (F_b == F_a).all(), d.nx
     finally:
@@ -102,7 +116,7 @@ def test_instances_joining_and_leaving_mid_run(mode):
         L.lbm_batch_run(b, 40)
         L.lbm_batch_synchronize(b)
         for d, s, g_done in ((d1, s1, None), (d2, s2, None), (d3, None, g3)):
-            g_a, F_a = _alone(d)
+            g_a, F_a = _alone(d, mode)
             if s is None:
                 assert (g_done == g_a).all()
                 continue
@@ -204,7 +218,7 @@ def test_damping_sweep_matches_direct_fit():
                            storage=L.LBM_STORE_F32)
     h = L.lbm_create(37, 128, 128, tau, omega, geom)
     try:
-        L.lbm_set_tile(h, 32, 4)
+        L.lbm_set_variant(h, 2)   # the batch's default kernel for D2Q37 FP32
         L.lbm_step(h, 4 * P)
         f_in, _, _ = L.lbm_fit(h, 2.0)
         direct = L.lbm_gamma_bar(h, f_in, 64.0)

@@ -74,7 +74,7 @@ def test_served_fit_matches_direct_fit():
     (res, hist), = _serve([r], [0.0])[0]
     h = L.lbm_create(37, 70, 41, 0.9, 0.05, r.desc.geom)
     try:
-        L.lbm_set_tile(h, 32, 4)
+        L.lbm_set_variant(h, 2)   # the kernel the server's batches run D2Q37 FP32 instances with
         L.lbm_step(h, 400)
         F = L.lbm_force_history(h)
         f_in, f_q, f_0 = L.lbm_fit(h, 2.0)
