@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -108,6 +109,14 @@ StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant) {
     if (Q != 37 || variant < 1 || variant > 2) return nullptr;
     return reinterpret_cast<StepLaunchFn>(storage <= ST_F32 ? find_occ_launcher_q37_wide(storage, coll, variant)
                                                             : find_occ_launcher_q37_half(storage, coll, variant));
+}
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("LBM_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 StepLaunchFn find_aa_launcher_q9(int storage, int coll, int phase);

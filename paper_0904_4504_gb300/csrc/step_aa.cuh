@@ -149,6 +149,7 @@ __device__ __forceinline__ void aa_local(const InstDev& P, ST* A, int x, int y, 
 // single buffer; force_out[0] and force_out[1] get the forces of steps n and n + 1 (PHASE 0 only).
 template <class L, class ST, int COLL, int PHASE>
 __global__ void __launch_bounds__(512) step_kernel_aa(const __grid_constant__ InstDev P) {
+    pdl_wait_then_release();
     const int tile = blockIdx.x;
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
@@ -166,8 +167,7 @@ __global__ void __launch_bounds__(512) step_kernel_aa(const __grid_constant__ In
 
 template <class L, class ST, int COLL, int PHASE>
 cudaError_t launch_step_aa(const InstDev& P, dim3 block, cudaStream_t stream) {
-    step_kernel_aa<L, ST, COLL, PHASE><<<P.ntiles, block, 0, stream>>>(P);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel_aa<L, ST, COLL, PHASE>, dim3(P.ntiles), block, 0, stream, P);
 }
 
 // Launcher of the in-place step for (lattice Q, storage, collision, phase); nullptr if not built.

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "lattice.cuh"
 
 namespace lbm {
@@ -74,6 +76,36 @@ struct InstDev {
     float Hl[37];
     float Hs[37];
 };
+
+// Programmatic dependent launch.  Step kernels are launched so that the next kernel of the stream
+// may be scheduled while this one drains: every step kernel first waits for the previous grid of
+// its stream to complete (its outputs are this step's inputs, including the force scratch), then
+// lets the next one launch.  The next grid is launched only after every block of this one has
+// passed that point, so its blocks never take SM slots that this grid still needs.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch a step kernel with programmatic stream serialization (disabled when the environment
+// sets LBM_PDL=0: plain stream order).
+bool pdl_enabled();
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // A launch constant in the arithmetic type T: the double itself, or its FP32 copy.
 template <class T>
@@ -532,6 +564,7 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
 // Single-instance step: one block per tile.
 template <class L, class ST, int COLL, int WALL = 0>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
+    pdl_wait_then_release();
     process_tile<L, ST, COLL, WALL>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
@@ -613,8 +646,7 @@ using BatchKernelFn = const void*;
 
 template <class L, class ST, int COLL, int WALL = 0>
 cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
-    step_kernel<L, ST, COLL, WALL><<<P.ntiles, block, 0, stream>>>(P);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel<L, ST, COLL, WALL>, dim3(P.ntiles), block, 0, stream, P);
 }
 
 // The plain step on 32 x 4 tiles with an occupancy floor: at least MINB blocks of 128 threads per
@@ -622,13 +654,13 @@ cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
 // kernel waits on its global loads; more resident warps hide more of that latency.
 template <class L, class ST, int COLL, int MINB>
 __global__ void __launch_bounds__(128, MINB) step_kernel_occ(const __grid_constant__ InstDev P) {
+    pdl_wait_then_release();
     process_tile<L, ST, COLL, 0>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
 template <class L, class ST, int COLL, int MINB>
 cudaError_t launch_step_occ(const InstDev& P, dim3 block, cudaStream_t stream) {
-    step_kernel_occ<L, ST, COLL, MINB><<<P.ntiles, block, 0, stream>>>(P);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel_occ<L, ST, COLL, MINB>, dim3(P.ntiles), block, 0, stream, P);
 }
 
 // Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.

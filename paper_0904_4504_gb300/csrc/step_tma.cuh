@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1(const __grid_constan
     using G = TmaGeom<L, ST, 1, BX, BY>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
+    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int x = (t % P.ntx) * BX + threadIdx.x;
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
     using T = typename S::CT;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
+    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int x = (t % P.ntx) * (2 * TX) + 2 * threadIdx.x;
@@ -348,8 +350,7 @@ cudaError_t launch_step_pair(const InstDev& P, const CUtensorMap& map, cudaStrea
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    step_kernel_pair<L, ST, COLL, TX, TY><<<P.ntiles, dim3(TX, TY), G::SMEM, stream>>>(P, map);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel_pair<L, ST, COLL, TX, TY>, dim3(P.ntiles), dim3(TX, TY), G::SMEM, stream, P, map);
 }
 
 using TmaStepLaunchFn = cudaError_t (*)(const InstDev& P, const CUtensorMap& map, cudaStream_t stream);
@@ -364,8 +365,7 @@ cudaError_t launch_step_tma1(const InstDev& P, const CUtensorMap& map, cudaStrea
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    step_kernel_tma1<L, ST, COLL, BX, BY><<<P.ntiles, dim3(BX, BY), G::SMEM, stream>>>(P, map);
-    return cudaGetLastError();
+    return launch_pdl(step_kernel_tma1<L, ST, COLL, BX, BY>, dim3(P.ntiles), dim3(BX, BY), G::SMEM, stream, P, map);
 }
 
 // Launch with one CTA per SM slot the kernel's shared memory allows (at most one per tile).
