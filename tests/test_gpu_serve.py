@@ -103,3 +103,20 @@ def test_request_larger_than_budget_is_rejected():
         assert e.value.code == L.LBM_ENOMEM
     finally:
         L.lbm_server_destroy(srv)
+
+
+def test_in_place_layout_doubles_what_a_budget_admits():
+    """The AA layout holds one population buffer: a budget that fits two two-buffer instances of a
+    2048^2 D2Q37 FP32 beam fits at least three in-place ones, and the results are those of the
+    two-buffer layout to FP32 rounding."""
+    kw = dict(lx=32, ly=32)
+    ab = [_req(37, 2048, 2048, 0.9, 0.05, 60, **kw) for _ in range(4)]
+    aa = [_req(37, 2048, 2048, 0.9, 0.05, 60, layout=L.LBM_LAYOUT_AA, **kw) for _ in range(4)]
+    budget = int(2.2 * L.lbm_batch_footprint(ab[0].desc))
+    assert 3 * L.lbm_batch_footprint(aa[0].desc) < budget
+    out_ab, st_ab = _serve(ab, [0.0] * 4, budget=budget, k=8)
+    out_aa, st_aa = _serve(aa, [0.0] * 4, budget=budget, k=8)
+    assert st_ab["peak_running"] == 2 and st_aa["peak_running"] >= 3
+    for (ra, ha), (rb, hb) in zip(out_aa, out_ab):
+        amp = np.abs(hb[:, 0]).max()
+        assert np.abs(ha[:, 0] - hb[:, 0]).max() <= 1e-5 * amp
