@@ -185,6 +185,8 @@ int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
  * (16-bit), the fastest single-instance kernels measured; lbm_set_tile selects variant 0.  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
  * copied to shared memory by bulk tensor copies (TMA), one box per direction plane:
  * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
+ * 13, 14: as 11, 12, with the outputs of interior tiles staged in shared memory and written by one
+ * bulk tensor store per direction plane (D2Q37);
  * 20, 21, 22: two neighbouring nodes per thread (paired loads and stores), tiles of 64 x 4,
  * 64 x 2 or 128 x 2 nodes (D2Q9: 10 and 20 only).
  * Every variant evaluates the same expressions in the same order; results agree to FP32 rounding

@@ -46,6 +46,8 @@ static bool variant_tile(int variant, int* bx, int* by) {
         case 10: *bx = 32; *by = 4; return true;
         case 11: *bx = 64; *by = 2; return true;
         case 12: *bx = 64; *by = 4; return true;
+        case 13: *bx = 64; *by = 2; return true;
+        case 14: *bx = 64; *by = 4; return true;
         case 20: *bx = 64; *by = 4; return true;
         case 21: *bx = 64; *by = 2; return true;
         case 22: *bx = 128; *by = 2; return true;
@@ -411,7 +413,8 @@ struct lbm_sim {
     TmaStepLaunchFn tma_launch = nullptr;
     bool aa = false;                   // in-place single buffer (LBM_LAYOUT_AA)
     StepLaunchFn aa_launch[2] = {nullptr, nullptr};  // even (pull-push) and odd (local) steps
-    CUtensorMap maps[2];
+    CUtensorMap maps[2];               // staged variants: load boxes of buffer k
+    CUtensorMap store_maps[2];         // variants 13, 14: the tile's own box in buffer k
     InstDev dev{};
 };
 
@@ -516,6 +519,15 @@ void stream_offset(const lbm_sim* s, double U, float* H, float* HM) {
     }
     if (HM)
         for (int k = 0; k < 6; ++k) HM[k] = (float)M[k];
+}
+
+// The same constants for the kernels: H_i depends on c_ix only, so they get it per c_ix (index
+// c_ix + 3), and the moments HM.
+void stream_offset_cx(const lbm_sim* s, double U, float* H7, float* HM) {
+    float H[37];
+    stream_offset(s, U, H, HM);
+    for (int k = 0; k < 7; ++k) H7[k] = 0.f;
+    for (int i = 0; i < s->lat.Q; ++i) H7[s->lat.c[i][0] + 3] = H[i];
 }
 
 int check_sim(lbm_sim* s) {
@@ -799,9 +811,12 @@ int lbm_set_variant(lbm_sim* s, int variant) {
         return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);
     tma_box(s->Q, s->geom.storage, bx, &bw, &pad);
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if ((rc = encode_map(&s->maps[k], s->buf[k], s->geom.storage, s->nx, s->ny, s->Q, s->pitch, bw, by)))
             return rc;
+        if ((rc = encode_map(&s->store_maps[k], s->buf[k], s->geom.storage, s->nx, s->ny, s->Q, s->pitch, bx, by)))
+            return rc;
+    }
     s->bx = bx;
     s->by = by;
     s->variant = variant;
@@ -829,8 +844,8 @@ int lbm_step(lbm_sim* s, long n) {
             s->dev.dv2_f = (float)s->dev.dv2;
             s->dev.stream_off = s->stream_off ? 1 : 0;
             if (s->stream_off) {
-                stream_offset(s, s->U_stream, s->dev.Hl, s->dev.HM);
-                stream_offset(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+                stream_offset_cx(s, s->U_stream, s->dev.Hl, s->dev.HM);
+                stream_offset_cx(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
             }
             s->dev.force_out = s->d_history + s->steps_done;
             const cudaError_t e = s->aa_launch[phase](s->dev, block, s->stream);
@@ -847,11 +862,11 @@ int lbm_step(lbm_sim* s, long n) {
         s->dev.dv_f = (float)s->dev.dv;
         s->dev.stream_off = s->stream_off ? 1 : 0;
         if (s->stream_off) {
-            stream_offset(s, s->U_stream, s->dev.Hl, s->dev.HM);
-            stream_offset(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+            stream_offset_cx(s, s->U_stream, s->dev.Hl, s->dev.HM);
+            stream_offset_cx(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
         }
         s->dev.force_out = s->d_history + s->steps_done;
-        const cudaError_t e = s->tma_launch ? s->tma_launch(s->dev, s->maps[s->cur], s->stream)
+        const cudaError_t e = s->tma_launch ? s->tma_launch(s->dev, s->maps[s->cur], s->store_maps[s->cur ^ 1], s->stream)
                                             : s->launch(s->dev, block, s->stream);
         if (e != cudaSuccess) return set_error(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         s->cur ^= 1;
@@ -1013,7 +1028,7 @@ int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
     if (steps < 1 || !n_out || (cap > 0 && !out)) return set_error(LBM_EINVAL, "need steps >= 1 and an output");
     // candidates: plain kernel tiles, then every staged variant built for this storage type
     const int tiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {32, 2}};
-    const int variants[] = {1, 2, 10, 11, 12, 20, 21, 22};
+    const int variants[] = {1, 2, 10, 11, 12, 13, 14, 20, 21, 22};
     std::vector<lbm_tune_entry> cand;
     for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
     for (int v : variants)

@@ -69,12 +69,13 @@ struct InstDev {
     float dv_f, rho0_f, s_f, inv_s_f, omega_c_f, reg_a_f, src_k_f, dv2_f;
     // 16-bit body-frame runs store h_i - H_i(n), with H_i(n) the (scaled) equilibrium deviation of
     // the uniform stream U(n) = sum_{k<n} g(k + 1/2) that the body force sets up; far from the body
-    // the stored values are then small and so are their rounding errors.  Hl: H of the state read,
-    // Hs: H of the state written, HM: moments sum_i w_i {1, c, cc} H_i of Hl (scaled units).
+    // the stored values are then small and so are their rounding errors.  The stream is along x, so
+    // H_i depends on c_ix only: Hl (the state read) and Hs (the state written) hold it for
+    // c_ix = -3..3 at index c_ix + 3.  HM: moments sum_i w_i {1, c, cc} H_i of Hl (scaled units).
     int stream_off;
     float HM[6];
-    float Hl[37];
-    float Hs[37];
+    float Hl[7];
+    float Hs[7];
 };
 
 // Programmatic dependent launch.  Step kernels are launched so that the next kernel of the stream
@@ -106,6 +107,12 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
+
+// Stream-offset constants of direction i (see InstDev): read / written state.
+template <class L>
+__device__ __forceinline__ float off_l(const InstDev& P, int i) { return P.Hl[cx_of<L>(i) + 3]; }
+template <class L>
+__device__ __forceinline__ float off_s(const InstDev& P, int i) { return P.Hs[cx_of<L>(i) + 3]; }
 
 // A launch constant in the arithmetic type T: the double itself, or its FP32 copy.
 template <class T>
@@ -237,7 +244,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
     const bool off = SCALED && P.stream_off;
     if (off && COLL == COLL_BGK) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) h[i] += (T)P.Hl[i];
+        for (int i = 0; i < Q; ++i) h[i] += (T)off_l<L>(P, i);
     }
     // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
     // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
@@ -249,7 +256,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
             if ((blk >> i) & 1ull) {
                 const int cx = cx_of<L>(i), cy = cy_of<L>(i);
                 T own = S::ld(src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx);
-                if (off) own += (T)P.Hl[opp_of<L>(i)];
+                if (off) own += (T)off_l<L>(P, opp_of<L>(i));
                 double mw = 0.0;
                 if ((lk.x >> i) & 1ull) {
                     if (P.moving) mw = P.mw_k * cx * dv;
@@ -261,7 +268,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
                 }
                 h[i] = own + (T)mw;
                 // the regularized path keeps h relative to the stream until the moments
-                if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
+                if (off && COLL == COLL_REG) h[i] -= (T)off_l<L>(P, i);
             }
         }
     } else if (WALL == 1 && cls == NODE_BOUNDARY && OWN == OWN_OPP) {
@@ -280,7 +287,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
             if ((blk >> i) & 1ull) {
                 const int wb = ((lk.x >> i) & 1ull) ? 0 : 1;
                 T own = S::ld(src + opp_of<L>(i) * plane + idx);
-                if (off) own += (T)P.Hl[opp_of<L>(i)];
+                if (off) own += (T)off_l<L>(P, opp_of<L>(i));
                 h[i] = own;  // kept until the second pass
                 const T w = (T)w_of<L>(i);
                 in[wb] += w * own;
@@ -322,7 +329,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
                     Fy -= cy * ws * hs;
                 }
                 h[i] = hadv;
-                if (off && COLL == COLL_REG) h[i] -= (T)P.Hl[i];
+                if (off && COLL == COLL_REG) h[i] -= (T)off_l<L>(P, i);
             }
         }
     }
@@ -442,6 +449,30 @@ __device__ __forceinline__ void eval_pair(const Coef<T>& C, int k, T hp, T hm, T
     }
 }
 
+// prepare + evaluation of one node; emit(i, v) receives output i in storage units (relative to the
+// stream offset when it is on).
+template <class L, class ST, int COLL, int WALL = 0, class Emit>
+__device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
+                                             float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
+                                             Emit&& emit) {
+    using T = typename StoreT<ST>::CT;
+    Coef<T> C;
+    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
+    const bool off = sizeof(ST) == 2 && P.stream_off;
+    emit(0, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)off_s<L>(P, 0) : (T)0));
+#pragma unroll
+    for (int k = 0; k < L::NP; ++k) {
+        T op, omn;
+        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
+        if (off) {
+            op -= (T)off_s<L>(P, 1 + 2 * k);
+            omn -= (T)off_s<L>(P, 2 + 2 * k);
+        }
+        emit(1 + 2 * k, op);
+        emit(2 + 2 * k, omn);
+    }
+}
+
 // prepare + evaluation + store of one node.
 template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
@@ -452,21 +483,8 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     ST* __restrict__ dst = static_cast<ST*>(dst_v);
     const long long plane = P.plane;
     const int idx = y * P.pitch + x;
-    Coef<T> C;
-    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
-    const bool off = sizeof(ST) == 2 && P.stream_off;
-    S::st(dst + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)P.Hs[0] : (T)0));
-#pragma unroll
-    for (int k = 0; k < L::NP; ++k) {
-        T op, omn;
-        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        if (off) {
-            op -= (T)P.Hs[1 + 2 * k];
-            omn -= (T)P.Hs[2 + 2 * k];
-        }
-        S::st(dst + (1 + 2 * k) * plane + idx, op);
-        S::st(dst + (2 + 2 * k) * plane + idx, omn);
-    }
+    collide_emit<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy,
+                                    [&](int i, T v) { S::st(dst + i * plane + idx, v); });
 }
 
 // Advection + wall + collision of the fluid node (x, y), sources from global memory.  WALL selects

@@ -51,7 +51,8 @@ void* find_occ_launcher_q37_wide(int storage, int coll, int variant) {
 }
 
 // Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10, 11, 12 = one
-// node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 20, 21, 22 = two nodes per thread on 64 x 4,
+// node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 13, 14 = the same on 64 x 2, 64 x 4 tiles with
+// the outputs stored through TMA; 20, 21, 22 = two nodes per thread on 64 x 4,
 // 64 x 2, 128 x 2 tiles.
 void* find_tma_launcher_q37_wide(int storage, int coll, int variant) {
     if (variant < 0 || variant >= 32) return nullptr;
@@ -62,6 +63,10 @@ void* find_tma_launcher_q37_wide(int storage, int coll, int variant) {
             return (void*)&launch_step_tma1<D2Q37, float, COLL_BGK, 64, 2>;
         case (ST_F32 * 2 + COLL_BGK) * 32 + 12:
             return (void*)&launch_step_tma1<D2Q37, float, COLL_BGK, 64, 4>;
+        case (ST_F32 * 2 + COLL_BGK) * 32 + 13:
+            return (void*)&launch_step_tma1s<D2Q37, float, COLL_BGK, 64, 2>;
+        case (ST_F32 * 2 + COLL_BGK) * 32 + 14:
+            return (void*)&launch_step_tma1s<D2Q37, float, COLL_BGK, 64, 4>;
         case (ST_F32 * 2 + COLL_BGK) * 32 + 20:
             return (void*)&launch_step_pair<D2Q37, float, COLL_BGK, 32, 4>;
         case (ST_F32 * 2 + COLL_BGK) * 32 + 21:
@@ -74,6 +79,10 @@ void* find_tma_launcher_q37_wide(int storage, int coll, int variant) {
             return (void*)&launch_step_tma1<D2Q37, float, COLL_REG, 64, 2>;
         case (ST_F32 * 2 + COLL_REG) * 32 + 12:
             return (void*)&launch_step_tma1<D2Q37, float, COLL_REG, 64, 4>;
+        case (ST_F32 * 2 + COLL_REG) * 32 + 13:
+            return (void*)&launch_step_tma1s<D2Q37, float, COLL_REG, 64, 2>;
+        case (ST_F32 * 2 + COLL_REG) * 32 + 14:
+            return (void*)&launch_step_tma1s<D2Q37, float, COLL_REG, 64, 4>;
         case (ST_F32 * 2 + COLL_REG) * 32 + 20:
             return (void*)&launch_step_pair<D2Q37, float, COLL_REG, 32, 4>;
         case (ST_F32 * 2 + COLL_REG) * 32 + 21:

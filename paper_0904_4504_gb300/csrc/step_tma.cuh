@@ -76,6 +76,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Bulk tensor store of one box from shared memory (tracked by the thread's bulk async-group).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+
 constexpr long long kTmaWaitLimit = 4000000000ll;  // clock cycles (about 2 s)
 
 // Tile t lies at least the lattice reach inside the grid (its boxes need no periodic wrap).
@@ -316,13 +324,13 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
         const long long plane = P.plane;
         const bool off = sizeof(ST) == 2 && P.stream_off;
         // solid nodes keep g = 0 (a stored 0 means h = H there; solid values are never read)
-        const T hs0 = off ? (T)P.Hs[0] : (T)0;
+        const T hs0 = off ? (T)off_s<L>(P, 0) : (T)0;
         S::st2(dst, f0 ? eval_rest<L, COLL, T>(C0, h0[0]) - hs0 : (T)0,
                f1 ? eval_rest<L, COLL, T>(C1, h1[0]) - hs0 : (T)0);
 #pragma unroll
         for (int k = 0; k < L::NP; ++k) {
             T p0 = 0, m0 = 0, p1 = 0, m1 = 0;
-            const T hp = off ? (T)P.Hs[1 + 2 * k] : (T)0, hm = off ? (T)P.Hs[2 + 2 * k] : (T)0;
+            const T hp = off ? (T)off_s<L>(P, 1 + 2 * k) : (T)0, hm = off ? (T)off_s<L>(P, 2 + 2 * k) : (T)0;
             if (f0) {
                 eval_pair<L, COLL, T>(C0, k, h0[1 + 2 * k], h0[2 + 2 * k], p0, m0);
                 p0 -= hp;
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
 }
 
 template <class L, class ST, int COLL, int TX, int TY>
-cudaError_t launch_step_pair(const InstDev& P, const CUtensorMap& map, cudaStream_t stream) {
+cudaError_t launch_step_pair(const InstDev& P, const CUtensorMap& map, const CUtensorMap&, cudaStream_t stream) {
     using G = TmaGeom<L, ST, 1, 2 * TX, TY>;
     static bool attr = false;
     if (!attr) {
@@ -353,10 +361,13 @@ cudaError_t launch_step_pair(const InstDev& P, const CUtensorMap& map, cudaStrea
     return launch_pdl(step_kernel_pair<L, ST, COLL, TX, TY>, dim3(P.ntiles), dim3(TX, TY), G::SMEM, stream, P, map);
 }
 
-using TmaStepLaunchFn = cudaError_t (*)(const InstDev& P, const CUtensorMap& map, cudaStream_t stream);
+// Launch of a staged step: `map` addresses the source buffer with the load boxes, `store_map` the
+// destination buffer with the tile's own box (used by the kernels that store through TMA).
+using TmaStepLaunchFn = cudaError_t (*)(const InstDev& P, const CUtensorMap& map, const CUtensorMap& store_map,
+                                        cudaStream_t stream);
 
 template <class L, class ST, int COLL, int BX, int BY>
-cudaError_t launch_step_tma1(const InstDev& P, const CUtensorMap& map, cudaStream_t stream) {
+cudaError_t launch_step_tma1(const InstDev& P, const CUtensorMap& map, const CUtensorMap&, cudaStream_t stream) {
     using G = TmaGeom<L, ST, 1, BX, BY>;
     static bool attr = false;
     if (!attr) {
@@ -368,9 +379,96 @@ cudaError_t launch_step_tma1(const InstDev& P, const CUtensorMap& map, cudaStrea
     return launch_pdl(step_kernel_tma1<L, ST, COLL, BX, BY>, dim3(P.ntiles), dim3(BX, BY), G::SMEM, stream, P, map);
 }
 
+// The staged step with staged stores: an interior tile's outputs are written to a second
+// shared-memory tile at compile-time offsets, then one thread stores each direction plane with one
+// bulk tensor copy (box BX x BY at the tile's origin, never negative, x a multiple of BX) and waits
+// for the copies before the block exits.  Nodes of the tile that are solid are stored as zero (no
+// step ever reads them).  Tiles at the periodic edges keep the plain loads and stores.
+template <class L, class ST, int COLL, int BX, int BY>
+struct TmaStoreGeom {
+    using G = TmaGeom<L, ST, 1, BX, BY>;
+    static constexpr int OSLOT = (BX * BY * (int)sizeof(ST) + 127) / 128 * 128;  // one plane of outputs
+    static constexpr int SMEM = G::SMEM + L::Q * OSLOT;
+};
+
+template <class L, class ST, int COLL, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY) step_kernel_tma1s(const __grid_constant__ InstDev P,
+                                                             const __grid_constant__ CUtensorMap map,
+                                                             const __grid_constant__ CUtensorMap smap) {
+    using G = TmaGeom<L, ST, 1, BX, BY>;
+    using O = TmaStoreGeom<L, ST, COLL, BX, BY>;
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
+    const int t = blockIdx.x;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int x = (t % P.ntx) * BX + threadIdx.x;
+    const int y = (t / P.ntx) * BY + threadIdx.y;
+    const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+    double Fx = 0.0, Fy = 0.0;
+    T h[L::Q];
+    if (tile_interior<G, L>(P, t)) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tile<G, L>(P, &map, t, smem, &bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(&bar, 0, kTmaWaitLimit);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(P.err, 4);
+                mbar_wait(&bar, 0, kTmaWaitLimit);
+            }
+            __syncthreads();
+            return;
+        }
+        unsigned char* out = smem + G::SMEM;
+        const int o = threadIdx.y * BX + threadIdx.x;
+        if (cls != NODE_SOLID) {
+            gather_smem<G, L, ST>(smem, threadIdx.x, threadIdx.y, h);
+            collide_emit<L, ST, COLL>(P, P.src, x, y, cls, P.dv, P.dv_f, h, Fx, Fy,
+                                      [&](int i, T v) { S::st(reinterpret_cast<ST*>(out + i * O::OSLOT) + o, v); });
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) S::st(reinterpret_cast<ST*>(out + i * O::OSLOT) + o, (T)0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy
+        __syncthreads();
+        if (tid == 0) {
+            const int x0 = (t % P.ntx) * BX, y0 = (t / P.ntx) * BY;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) tma_store_3d(&smap, x0, y0, i, out + i * O::OSLOT);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+    } else if (cls != NODE_SOLID) {
+        gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
+        collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, h, Fx, Fy);
+    }
+    tile_epilogue(P, t, P.force_out, Fx, Fy);
+}
+
+template <class L, class ST, int COLL, int BX, int BY>
+cudaError_t launch_step_tma1s(const InstDev& P, const CUtensorMap& map, const CUtensorMap& smap,
+                              cudaStream_t stream) {
+    using O = TmaStoreGeom<L, ST, COLL, BX, BY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_tma1s<L, ST, COLL, BX, BY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, O::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(step_kernel_tma1s<L, ST, COLL, BX, BY>, dim3(P.ntiles), dim3(BX, BY), O::SMEM, stream, P, map,
+                      smap);
+}
+
 // Launch with one CTA per SM slot the kernel's shared memory allows (at most one per tile).
 template <class L, class ST, int COLL, int STAGES>
-cudaError_t launch_step_tma(const InstDev& P, const CUtensorMap& map, cudaStream_t stream) {
+cudaError_t launch_step_tma(const InstDev& P, const CUtensorMap& map, const CUtensorMap&, cudaStream_t stream) {
     using G = TmaGeom<L, ST, STAGES>;
     static int grid_cap = 0;  // per instantiation: SMs x resident CTAs
     if (!grid_cap) {

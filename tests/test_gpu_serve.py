@@ -110,8 +110,8 @@ def test_in_place_layout_doubles_what_a_budget_admits():
     2048^2 D2Q37 FP32 beam fits at least three in-place ones, and the results are those of the
     two-buffer layout to FP32 rounding."""
     kw = dict(lx=32, ly=32)
-    ab = [_req(37, 2048, 2048, 0.9, 0.05, 60, **kw) for _ in range(4)]
-    aa = [_req(37, 2048, 2048, 0.9, 0.05, 60, layout=L.LBM_LAYOUT_AA, **kw) for _ in range(4)]
+    ab = [_req(37, 2048, 2048, 0.9, 0.2, 60, **kw) for _ in range(4)]     # 60 steps: 1.9 periods
+    aa = [_req(37, 2048, 2048, 0.9, 0.2, 60, layout=L.LBM_LAYOUT_AA, **kw) for _ in range(4)]
     budget = int(2.2 * L.lbm_batch_footprint(ab[0].desc))
     assert 3 * L.lbm_batch_footprint(aa[0].desc) < budget
     out_ab, st_ab = _serve(ab, [0.0] * 4, budget=budget, k=8)
