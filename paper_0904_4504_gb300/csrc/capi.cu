@@ -530,6 +530,14 @@ void stream_offset_cx(const lbm_sim* s, double U, float* H7, float* HM) {
     for (int i = 0; i < s->lat.Q; ++i) H7[s->lat.c[i][0] + 3] = H[i];
 }
 
+// Even and odd parts in c_x of the stored state's offsets, for m = |c_x| (see InstDev).
+void stream_offset_eo(const float* H7, float* He, float* Ho) {
+    for (int m = 0; m < 4; ++m) {
+        He[m] = 0.5f * (H7[3 + m] + H7[3 - m]);
+        Ho[m] = 0.5f * (H7[3 + m] - H7[3 - m]);
+    }
+}
+
 int check_sim(lbm_sim* s) {
     if (!s) return set_error(LBM_EINVAL, "null simulation");
     CUDA_TRY(cudaSetDevice(s->device));
@@ -846,6 +854,7 @@ int lbm_step(lbm_sim* s, long n) {
             if (s->stream_off) {
                 stream_offset_cx(s, s->U_stream, s->dev.Hl, s->dev.HM);
                 stream_offset_cx(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+                stream_offset_eo(s->dev.Hs, s->dev.He, s->dev.Ho);
             }
             s->dev.force_out = s->d_history + s->steps_done;
             const cudaError_t e = s->aa_launch[phase](s->dev, block, s->stream);
@@ -864,6 +873,7 @@ int lbm_step(lbm_sim* s, long n) {
         if (s->stream_off) {
             stream_offset_cx(s, s->U_stream, s->dev.Hl, s->dev.HM);
             stream_offset_cx(s, s->U_stream + s->dev.dv, s->dev.Hs, nullptr);
+            stream_offset_eo(s->dev.Hs, s->dev.He, s->dev.Ho);
         }
         s->dev.force_out = s->d_history + s->steps_done;
         const cudaError_t e = s->tma_launch ? s->tma_launch(s->dev, s->maps[s->cur], s->store_maps[s->cur ^ 1], s->stream)

@@ -84,7 +84,8 @@ extern "C" int lbm_step_noalloc(const lbm_sim* sim, long n, const void* g_in, vo
     P.force_out = reinterpret_cast<double2*>(force_out);
     P.dv = drive_value(v.drive, v.u0, v.omega, n);
     P.dv_f = (float)P.dv;
-    P.stream_off = 0;  // caller buffers hold plain scaled deviations
+    P.stream_off = 0;  // caller buffers hold plain scaled deviations: no offsets
+    for (int m = 0; m < 4; ++m) P.He[m] = P.Ho[m] = 0.f;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the ticket must start at zero (a completed call leaves it at zero; this also covers a call
     // that never completed); the partials are always written before they are read

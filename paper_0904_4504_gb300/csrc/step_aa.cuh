@@ -62,25 +62,27 @@ __device__ __forceinline__ void aa_push(const InstDev& P, ST* A, int idx, const 
     if (BND) lk = P.links[idx];
     const unsigned long long blk = lk.x | lk.y;
 
-    auto push = [&](int i, T o) {
+    // v: output i relative to the stored state's stream offset (16-bit), as eval_pair returns it
+    auto push = [&](int i, T v) {
         const int j = opp_of<L>(i);
         if (BND && ((blk >> j) & 1ull)) {
             double mw = 0.0;
+            const T hi = off ? (T)off_s<L>(P, i) : (T)0;
             if ((lk.x >> j) & 1ull) {
                 if (P.moving) mw = P.mw_k * cx_of<L>(j) * P.dv2;
-                // the value the two-buffer step would read back: o rounded to the storage type
-                const T own = S::rnd(o - (off ? (T)off_s<L>(P, i) : (T)0)) + (off ? (T)off_s<L>(P, i) : (T)0);
+                // the value the two-buffer step would read back: v rounded to the storage type
+                const T own = S::rnd(v) + hi;
                 const double hs = 2.0 * (double)own + mw;
                 const double ws = w_of<L>(j) * P.s;
                 Gx -= cx_of<L>(j) * ws * hs;
                 Gy -= cy_of<L>(j) * ws * hs;
             }
-            S::st(A + j * plane + idx, o + (T)mw - (off ? (T)off_s<L>(P, j) : (T)0));
+            S::st(A + j * plane + idx, v + hi + (T)mw - (off ? (T)off_s<L>(P, j) : (T)0));
         } else {
-            S::st(A + i * plane + roff[R - cy_of<L>(i)] + col[R - cx_of<L>(i)], o - (off ? (T)off_s<L>(P, i) : (T)0));
+            S::st(A + i * plane + roff[R - cy_of<L>(i)] + col[R - cx_of<L>(i)], v);
         }
     };
-    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)off_s<L>(P, 0) : (T)0));
+    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]));
 #pragma unroll
     for (int k = 0; k < L::NP; ++k) {
         T op, omn;
@@ -134,14 +136,13 @@ __device__ __forceinline__ void aa_local(const InstDev& P, ST* A, int x, int y, 
     Coef<T> C;
     double Fx = 0.0, Fy = 0.0;  // no fix-up on this step: stays zero
     prepare<L, ST, COLL, 0, OWN_NONE>(P, A, x, y, cls, P.dv, P.dv_f, h, Fx, Fy, C);
-    const bool off = sizeof(ST) == 2 && P.stream_off;
-    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)off_s<L>(P, 0) : (T)0));
+    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]));
 #pragma unroll
     for (int k = 0; k < L::NP; ++k) {
         T op, omn;
         eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        S::st(A + (2 + 2 * k) * plane + idx, op - (off ? (T)off_s<L>(P, 1 + 2 * k) : (T)0));
-        S::st(A + (1 + 2 * k) * plane + idx, omn - (off ? (T)off_s<L>(P, 2 + 2 * k) : (T)0));
+        S::st(A + (2 + 2 * k) * plane + idx, op);
+        S::st(A + (1 + 2 * k) * plane + idx, omn);
     }
 }
 

@@ -72,10 +72,16 @@ struct InstDev {
     // the stored values are then small and so are their rounding errors.  The stream is along x, so
     // H_i depends on c_ix only: Hl (the state read) and Hs (the state written) hold it for
     // c_ix = -3..3 at index c_ix + 3.  HM: moments sum_i w_i {1, c, cc} H_i of Hl (scaled units).
+    // He, Ho: the even and odd parts of Hs in c_x, He[m] = (Hs(m) + Hs(-m)) / 2 and
+    // Ho[m] = (Hs(m) - Hs(-m)) / 2 for m = |c_x|; the collision folds them into its per-node
+    // coefficients, so outputs leave it already relative to the stream.  All zero when stream_off
+    // is clear.
     int stream_off;
     float HM[6];
     float Hl[7];
     float Hs[7];
+    float He[4];
+    float Ho[4];
 };
 
 // Programmatic dependent launch.  Step kernels are launched so that the next kernel of the stream
@@ -217,6 +223,9 @@ struct Coef {
     T rxx, rxy, ryy, hf;       // regularized part and first-order force part
     T kf, inv_s;               // force coefficient, 1/s
     T om, e0, kfu;             // plain BGK: 1/tau, equilibrium constant, even source constant
+    // per m = |c_x| (0..3), with the stream offset of the stored state folded in (16-bit storage):
+    // regularized: c0 - He[m] and m hf - Ho[m]; plain BGK: kfu - He[m] and m kf - Ho[m]
+    T ce[4], co[4];
 };
 
 // Bounce-back (fix-up of h on blocked links), moments and collision coefficients of the fluid node
@@ -410,39 +419,50 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
         C.rxx *= is; C.rxy *= is; C.ryy *= is; C.kf *= is; C.hf *= is;
         C.e0 *= is; C.kfu *= is;
     }
+    // constant parts of the outputs per m = |c_x|; 16-bit storage subtracts the stream offset of
+    // the stored state here, once per node (He, Ho are zero when it is off)
+    const T cbase = COLL == COLL_REG ? C.c0 : C.kfu, obase = COLL == COLL_REG ? C.hf : C.kf;
+#pragma unroll
+    for (int m = 0; m <= L::R; ++m) {
+        C.ce[m] = SCALED ? cbase - (T)P.He[m] : cbase;
+        C.co[m] = SCALED ? (T)m * obase - (T)P.Ho[m] : (T)m * obase;
+    }
 }
 
 // Output of the rest direction, in storage units (the coefficients already carry 1/s).
 template <class L, int COLL, class T>
 __device__ __forceinline__ T eval_rest(const Coef<T>& C, T h0) {
-    if (COLL == COLL_REG) return C.c0;
-    return h0 + C.om * (C.e0 - h0) + C.kfu;
+    if (COLL == COLL_REG) return C.ce[0];
+    return h0 + C.om * (C.e0 - h0) + C.ce[0];
 }
 
-// Outputs of pair k (+p_k, -p_k), in storage units; hp, hm are the pulled populations (BGK only).
+// Outputs of pair k (+p_k, -p_k), in storage units and relative to the stored state's stream
+// offset (16-bit); hp, hm are the pulled populations (BGK only).  The pair tables have p_kx >= 0,
+// so m = p_kx indexes the per-|c_x| constants.
 template <class L, int COLL, class T>
 __device__ __forceinline__ void eval_pair(const Coef<T>& C, int k, T hp, T hm, T& op, T& omn) {
     const int px = L::px(k), py = L::py(k);
+    static_assert(L::px(0) >= 0, "pairs are listed with p_x >= 0");
     T a = 0;
     if (px) a += (T)px * C.ax;
     if (py) a += (T)py * C.ay;
     const T a2 = a * a;
     if (COLL == COLL_REG) {
-        T E = C.c0 + a2 * (C.e1 + a2 * C.e2);
+        T E = C.ce[px] + a2 * (C.e1 + a2 * C.e2);
         if (px) E += (T)(px * px) * C.rxx;
         if (px && py) E += (T)(px * py) * C.rxy;
         if (py) E += (T)(py * py) * C.ryy;
         if (px) E += a * ((T)px * C.kf);
-        T O = a * (C.o0 + C.o1 * a2);
-        if (px) O += (T)px * C.hf;
+        const T O = a * (C.o0 + C.o1 * a2) + C.co[px];
         // Eq. 18: f = f^eq + (1 - 1/tau) f^ne (+ source)
         op = E + O;
         omn = E - O;
     } else {
         const T E = C.e0 + a2 * (C.e1 + a2 * C.e2);
         const T O = a * (C.o0 + C.o1 * a2);
-        T Es = C.kfu, Os = 0;
-        if (px) { Es += a * ((T)px * C.kf); Os = (T)px * C.kf; }
+        T Es = C.ce[px];
+        if (px) Es += a * ((T)px * C.kf);
+        const T Os = C.co[px];
         // Eq. 14 discretized: f - (f - f^eq)/tau + source
         op = hp + C.om * ((E + O) - hp) + (Es + Os);
         omn = hm + C.om * ((E - O) - hm) + (Es - Os);
@@ -458,16 +478,11 @@ __device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v
     using T = typename StoreT<ST>::CT;
     Coef<T> C;
     prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
-    const bool off = sizeof(ST) == 2 && P.stream_off;
-    emit(0, eval_rest<L, COLL, T>(C, h[0]) - (off ? (T)off_s<L>(P, 0) : (T)0));
+    emit(0, eval_rest<L, COLL, T>(C, h[0]));
 #pragma unroll
     for (int k = 0; k < L::NP; ++k) {
         T op, omn;
         eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        if (off) {
-            op -= (T)off_s<L>(P, 1 + 2 * k);
-            omn -= (T)off_s<L>(P, 2 + 2 * k);
-        }
         emit(1 + 2 * k, op);
         emit(2 + 2 * k, omn);
     }

@@ -322,25 +322,13 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
         const bool f0 = cls0 != NODE_SOLID, f1 = cls1 != NODE_SOLID;
         ST* __restrict__ dst = static_cast<ST*>(P.dst) + y * P.pitch + x;
         const long long plane = P.plane;
-        const bool off = sizeof(ST) == 2 && P.stream_off;
         // solid nodes keep g = 0 (a stored 0 means h = H there; solid values are never read)
-        const T hs0 = off ? (T)off_s<L>(P, 0) : (T)0;
-        S::st2(dst, f0 ? eval_rest<L, COLL, T>(C0, h0[0]) - hs0 : (T)0,
-               f1 ? eval_rest<L, COLL, T>(C1, h1[0]) - hs0 : (T)0);
+        S::st2(dst, f0 ? eval_rest<L, COLL, T>(C0, h0[0]) : (T)0, f1 ? eval_rest<L, COLL, T>(C1, h1[0]) : (T)0);
 #pragma unroll
         for (int k = 0; k < L::NP; ++k) {
             T p0 = 0, m0 = 0, p1 = 0, m1 = 0;
-            const T hp = off ? (T)off_s<L>(P, 1 + 2 * k) : (T)0, hm = off ? (T)off_s<L>(P, 2 + 2 * k) : (T)0;
-            if (f0) {
-                eval_pair<L, COLL, T>(C0, k, h0[1 + 2 * k], h0[2 + 2 * k], p0, m0);
-                p0 -= hp;
-                m0 -= hm;
-            }
-            if (f1) {
-                eval_pair<L, COLL, T>(C1, k, h1[1 + 2 * k], h1[2 + 2 * k], p1, m1);
-                p1 -= hp;
-                m1 -= hm;
-            }
+            if (f0) eval_pair<L, COLL, T>(C0, k, h0[1 + 2 * k], h0[2 + 2 * k], p0, m0);
+            if (f1) eval_pair<L, COLL, T>(C1, k, h1[1 + 2 * k], h1[2 + 2 * k], p1, m1);
             S::st2(dst + (1 + 2 * k) * plane, p0, p1);
             S::st2(dst + (2 + 2 * k) * plane, m0, m1);
         }
