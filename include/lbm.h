@@ -181,14 +181,17 @@ int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
 /* Choose the step kernel.  0: plain kernel, one block per tile of lbm_set_tile's shape, wrapped
  * global loads.  1, 2: the plain kernel on 32 x 4 tiles compiled for at least 6 (1) or 7 (2)
  * resident blocks per SM (fewer registers, more warps to hide load latency; D2Q37, FP32/BF16/FP16
- * storage).  lbm_create starts D2Q37 two-buffer bounce-back runs on variant 1 (FP32) or 2
- * (16-bit), the fastest single-instance kernels measured; lbm_set_tile selects variant 0.  Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are
- * copied to shared memory by bulk tensor copies (TMA), one box per direction plane:
+ * storage); 3, 4: 7 blocks per SM, each thread computing 2 or 4 nodes of its column (tiles of
+ * 32 x 8 or 32 x 16 nodes).  lbm_create starts D2Q37 two-buffer bounce-back runs on variant 1 (FP32) or 2
+ * (16-bit), the fastest single-instance kernels measured; lbm_set_tile selects variant 0.
+ * Staged kernels (FP32/BF16/FP16 storage), whose interior tiles are copied to shared memory by
+ * bulk tensor copies (TMA), one box per direction plane:
  * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
- * 13, 14: as 11, 12, with the outputs of interior tiles staged in shared memory and written by one
- * bulk tensor store per direction plane (D2Q37);
- * 20, 21, 22: two neighbouring nodes per thread (paired loads and stores), tiles of 64 x 4,
- * 64 x 2 or 128 x 2 nodes (D2Q9: 10 and 20 only).
+ * 13: as 11, with the outputs of interior tiles staged in shared memory and written by one bulk
+ * tensor store per direction plane (D2Q37);
+ * 18, 23, 24, 25: several nodes per thread, one row apart, on blocks of 64 x 1 (4 rows, at least 12
+ * blocks per SM), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks), 128 x 1 (2 rows) threads (D2Q37);
+ * 20: two neighbouring nodes per thread with paired loads and stores, 64 x 4 tiles (D2Q9).
  * Every variant evaluates the same expressions in the same order; results agree to FP32 rounding
  * (the compiler may contract them into different fused multiply-adds in different kernels) and the
  * force also by the order in which tile partials are summed when the tile shape differs.
@@ -299,8 +302,8 @@ int lbm_batch_remove(lbm_batch* batch, int slot);
 int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
- * numbers; -1, the default: the staged variant 11 for 16-bit storage, variant 2 for D2Q37 FP32,
- * else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
+ * numbers; -1, the default: for D2Q37 the staged variant 24 with 16-bit storage and variant 2 with
+ * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
  * support falls back to the plain kernel.  Ignored by the persistent mode.  LBM_EINVAL for a number
  * below -1. */
 int lbm_batch_set_variant(lbm_batch* batch, int variant);

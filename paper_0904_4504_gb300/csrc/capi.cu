@@ -24,17 +24,42 @@
 namespace lbm {
 
 void* find_tma_launcher_q9(int storage, int coll, int variant);
-void* find_tma_launcher_q37_wide(int storage, int coll, int variant);
-void* find_tma_launcher_q37_half(int storage, int coll, int variant);
 void tma_box_q9(int storage, int bx, int* bw, int* pad);
-void tma_box_q37_wide(int storage, int bx, int* bw, int* pad);
-void tma_box_q37_half(int storage, int bx, int* bw, int* pad);
+
+// D2Q37 launch tables, one translation unit per storage type (step_q37_inst.cuh).
+#define LBM_Q37_DECLS(SFX)                                          \
+    void* find_launcher_q37_##SFX(int coll, bool batched);          \
+    void* find_launcher_q37_##SFX##_ds(int coll);                   \
+    void* find_occ_launcher_q37_##SFX(int coll, int variant);       \
+    void* find_tma_launcher_q37_##SFX(int coll, int variant);       \
+    void tma_box_q37_##SFX(int bx, int* bw, int* pad);
+LBM_Q37_DECLS(f64)
+LBM_Q37_DECLS(f32)
+LBM_Q37_DECLS(bf16)
+LBM_Q37_DECLS(f16)
+#undef LBM_Q37_DECLS
+
+struct Q37Table {
+    void* (*plain)(int coll, bool batched);
+    void* (*plain_ds)(int coll);
+    void* (*occ)(int coll, int variant);
+    void* (*tma)(int coll, int variant);
+    void (*box)(int bx, int* bw, int* pad);
+};
+
+static const Q37Table* q37_table(int storage) {
+#define LBM_Q37_ROW(SFX)                                                                          \
+    {find_launcher_q37_##SFX, find_launcher_q37_##SFX##_ds, find_occ_launcher_q37_##SFX,          \
+     find_tma_launcher_q37_##SFX, tma_box_q37_##SFX}
+    static const Q37Table rows[4] = {LBM_Q37_ROW(f64), LBM_Q37_ROW(f32), LBM_Q37_ROW(bf16), LBM_Q37_ROW(f16)};
+#undef LBM_Q37_ROW
+    return storage >= ST_F64 && storage <= ST_F16 ? &rows[storage] : nullptr;
+}
 
 static TmaStepLaunchFn find_tma_launcher(int Q, int storage, int coll, int variant) {
     void* f = nullptr;
     if (Q == 9) f = find_tma_launcher_q9(storage, coll, variant);
-    else if (Q == 37 && storage == ST_F32) f = find_tma_launcher_q37_wide(storage, coll, variant);
-    else if (Q == 37) f = find_tma_launcher_q37_half(storage, coll, variant);
+    else if (Q == 37 && q37_table(storage)) f = q37_table(storage)->tma(coll, variant);
     return reinterpret_cast<TmaStepLaunchFn>(f);
 }
 
@@ -44,10 +69,15 @@ static bool variant_tile(int variant, int* bx, int* by) {
         case 1:
         case 2:
         case 10: *bx = 32; *by = 4; return true;
+        case 3: *bx = 32; *by = 8; return true;
+        case 4: *bx = 32; *by = 16; return true;
         case 11: *bx = 64; *by = 2; return true;
         case 12: *bx = 64; *by = 4; return true;
         case 13: *bx = 64; *by = 2; return true;
-        case 14: *bx = 64; *by = 4; return true;
+        case 18: *bx = 64; *by = 4; return true;
+        case 23: *bx = 64; *by = 2; return true;
+        case 24: *bx = 64; *by = 4; return true;
+        case 25: *bx = 128; *by = 2; return true;
         case 20: *bx = 64; *by = 4; return true;
         case 21: *bx = 64; *by = 2; return true;
         case 22: *bx = 128; *by = 2; return true;
@@ -58,8 +88,7 @@ static bool variant_tile(int variant, int* bx, int* by) {
 static void tma_box(int Q, int storage, int bx, int* bw, int* pad) {
     *bw = *pad = 0;
     if (Q == 9) tma_box_q9(storage, bx, bw, pad);
-    else if (Q == 37 && storage == ST_F32) tma_box_q37_wide(storage, bx, bw, pad);
-    else if (Q == 37) tma_box_q37_half(storage, bx, bw, pad);
+    else if (Q == 37 && q37_table(storage)) q37_table(storage)->box(bx, bw, pad);
 }
 
 // Tensor map of one population buffer: 3-D (x, y, direction), boxes of bw x by x 1.
@@ -92,25 +121,16 @@ static int encode_map(CUtensorMap* map, void* base, int storage, int nx, int ny,
 
 void* find_launcher_q9(int storage, int coll, bool batched);
 void* find_launcher_q9_ds(int storage, int coll);
-void* find_launcher_q37_wide_ds(int storage, int coll);
-void* find_launcher_q37_half_ds(int storage, int coll);
-void* find_launcher_q37_wide(int storage, int coll, bool batched);
-void* find_launcher_q37_half(int storage, int coll, bool batched);
 
 static void* find_launcher(int Q, int storage, int coll, bool batched) {
     if (Q == 9) return find_launcher_q9(storage, coll, batched);
-    if (Q == 37) return storage <= ST_F32 ? find_launcher_q37_wide(storage, coll, batched)
-                                          : find_launcher_q37_half(storage, coll, batched);
+    if (Q == 37 && q37_table(storage)) return q37_table(storage)->plain(coll, batched);
     return nullptr;
 }
 
-void* find_occ_launcher_q37_wide(int storage, int coll, int variant);
-void* find_occ_launcher_q37_half(int storage, int coll, int variant);
-
 StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant) {
-    if (Q != 37 || variant < 1 || variant > 2) return nullptr;
-    return reinterpret_cast<StepLaunchFn>(storage <= ST_F32 ? find_occ_launcher_q37_wide(storage, coll, variant)
-                                                            : find_occ_launcher_q37_half(storage, coll, variant));
+    if (Q != 37 || variant < 1 || variant > 4 || !q37_table(storage)) return nullptr;
+    return reinterpret_cast<StepLaunchFn>(q37_table(storage)->occ(coll, variant));
 }
 
 bool pdl_enabled() {
@@ -136,8 +156,7 @@ StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall) {
     if (wall == 0) return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
     void* f = nullptr;
     if (Q == 9) f = find_launcher_q9_ds(storage, coll);
-    else if (Q == 37 && storage <= ST_F32) f = find_launcher_q37_wide_ds(storage, coll);
-    else if (Q == 37) f = find_launcher_q37_half_ds(storage, coll);
+    else if (Q == 37 && q37_table(storage)) f = q37_table(storage)->plain_ds(coll);
     return reinterpret_cast<StepLaunchFn>(f);
 }
 BatchKernelFn find_batch_kernel(int Q, int storage, int coll) {
@@ -691,6 +710,10 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     const int align = (int)(128 / es);
     s->pitch = (nx + align - 1) / align * align;
     const size_t plane = (size_t)ny * s->pitch;
+    if ((size_t)H.Q * plane >= (1ull << 32)) {  // the kernels address populations with 32-bit offsets
+        delete s;
+        return set_error(LBM_EINVAL, "grid %dx%d: %d x %zu populations exceed 2^32", nx, ny, H.Q, plane);
+    }
 
     if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
@@ -802,12 +825,11 @@ int lbm_set_variant(lbm_sim* s, int variant) {
     if (s->aa) return set_error(LBM_EINVAL, "the in-place (AA) layout runs the plain kernel (variant 0) only");
     if (s->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
         return set_error(LBM_EINVAL, "kernel variants are built for bounce-back walls only");
-    if (variant == 1 || variant == 2) {
+    if (variant >= 1 && variant <= 4) {
         StepLaunchFn f = find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
         if (!f) return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);
         CUDA_TRY(cudaStreamSynchronize(s->stream));
-        s->bx = 32;
-        s->by = 4;
+        variant_tile(variant, &s->bx, &s->by);
         s->variant = variant;
         s->tma_launch = nullptr;
         s->launch = f;
@@ -1038,7 +1060,7 @@ int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
     if (steps < 1 || !n_out || (cap > 0 && !out)) return set_error(LBM_EINVAL, "need steps >= 1 and an output");
     // candidates: plain kernel tiles, then every staged variant built for this storage type
     const int tiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {32, 2}};
-    const int variants[] = {1, 2, 10, 11, 12, 13, 14, 20, 21, 22};
+    const int variants[] = {1, 2, 3, 4, 10, 11, 12, 13, 18, 20, 23, 24, 25};
     std::vector<lbm_tune_entry> cand;
     for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
     for (int v : variants)

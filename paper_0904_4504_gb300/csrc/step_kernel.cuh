@@ -194,8 +194,8 @@ __device__ __forceinline__ void gather_global(const InstDev& P, const ST* __rest
                                               typename StoreT<ST>::CT (&h)[L::Q]) {
     using S = StoreT<ST>;
     constexpr int Q = L::Q, R = L::R;
-    const long long plane = P.plane;
-    int roff[2 * R + 1], col[2 * R + 1];
+    const unsigned plane = (unsigned)P.plane;  // Q * plane < 2^32 (checked at creation)
+    unsigned roff[2 * R + 1], col[2 * R + 1];
 #pragma unroll
     for (int d = -R; d <= R; ++d) {
         int ys = y - d;
@@ -204,13 +204,14 @@ __device__ __forceinline__ void gather_global(const InstDev& P, const ST* __rest
         int xs = x - d;
         xs += xs < 0 ? P.nx : 0;
         xs -= xs >= P.nx ? P.nx : 0;
-        roff[d + R] = ys * P.pitch;
-        col[d + R] = xs;
+        roff[d + R] = (unsigned)(ys * P.pitch);
+        col[d + R] = (unsigned)xs;
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-        h[i] = S::ld(src + i * plane + roff[cy + R] + col[cx + R]);
+        // 32-bit element offset, widened once: one multiply-add per address
+        h[i] = S::ld(src + (unsigned)(i * plane + roff[cy + R] + col[cx + R]));
     }
 }
 
@@ -495,11 +496,12 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
                                               double& Fy) {
     using S = StoreT<ST>;
     using T = typename S::CT;
-    ST* __restrict__ dst = static_cast<ST*>(dst_v);
-    const long long plane = P.plane;
-    const int idx = y * P.pitch + x;
+    // 32-bit plane stride (Q * plane < 2^32, checked at creation): each address is the node's
+    // pointer plus stride * i, one widening multiply-add
+    ST* __restrict__ dst = static_cast<ST*>(dst_v) + (y * P.pitch + x);
+    const unsigned plane = (unsigned)P.plane;
     collide_emit<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy,
-                                    [&](int i, T v) { S::st(dst + i * plane + idx, v); });
+                                    [&](int i, T v) { S::st(dst + (unsigned long long)plane * (unsigned)i, v); });
 }
 
 // Advection + wall + collision of the fluid node (x, y), sources from global memory.  WALL selects
@@ -696,9 +698,34 @@ cudaError_t launch_step_occ(const InstDev& P, dim3 block, cudaStream_t stream) {
     return launch_pdl(step_kernel_occ<L, ST, COLL, MINB>, dim3(P.ntiles), block, 0, stream, P);
 }
 
+// The same on tiles of 32 x (4 NR) nodes: each thread computes NR nodes of its column, 4 rows apart,
+// one at a time, so that the block's fixed costs (tile indices, launch constants, the force
+// epilogue) are spread over NR nodes.
+template <class L, class ST, int COLL, int MINB, int NR>
+__global__ void __launch_bounds__(128, MINB) step_kernel_occn(const __grid_constant__ InstDev P) {
+    pdl_wait_then_release();
+    const int t = blockIdx.x;
+    const int x = (t % P.ntx) * 32 + threadIdx.x;
+    const int y0 = (t / P.ntx) * (4 * NR) + threadIdx.y;
+    double Fx = 0.0, Fy = 0.0;
+#pragma unroll 1
+    for (int r = 0; r < NR; ++r) {
+        const int y = y0 + 4 * r;
+        const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+        if (cls != NODE_SOLID) node_update<L, ST, COLL, 0>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, Fx, Fy);
+    }
+    tile_epilogue(P, t, P.force_out, Fx, Fy);
+}
+
+template <class L, class ST, int COLL, int MINB, int NR>
+cudaError_t launch_step_occn(const InstDev& P, dim3, cudaStream_t stream) {
+    return launch_pdl(step_kernel_occn<L, ST, COLL, MINB, NR>, dim3(P.ntiles), dim3(32, 4), 0, stream, P);
+}
+
 // Launchers for (lattice Q, storage, collision); nullptr if the combination is not built.
 StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall = 0);
-// Plain step with an occupancy floor: variant 1 = 6 blocks of 128 per SM, 2 = 7 (nullptr if not built).
+// Plain step with an occupancy floor: variant 1 = 6 blocks of 128 per SM, 2 = 7; 3, 4 = 7 blocks with
+// 2 or 4 nodes per thread (nullptr if not built).
 StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant);
 // Address of batch_kernel<...> for a cooperative launch (nullptr if not built).
 BatchKernelFn find_batch_kernel(int Q, int storage, int coll);

@@ -1,0 +1,96 @@
+// D2Q37 launch tables for one storage type: each of step_q37_f64.cu, step_q37_f32.cu,
+// step_q37_bf16.cu and step_q37_f16.cu instantiates them for its type (four translation units that
+// compile in parallel).  Variant numbers are those of lbm_set_variant.
+#pragma once
+
+#include "step_tma.cuh"
+
+namespace lbm {
+
+// Plain step (or the persistent batch kernel), bounce-back walls.
+template <class ST>
+void* q37_plain(int coll, bool batched) {
+    if (coll == COLL_REG)
+        return batched ? (void*)&batch_kernel<D2Q37, ST, COLL_REG> : (void*)&launch_step<D2Q37, ST, COLL_REG>;
+    if (coll == COLL_BGK)
+        return batched ? (void*)&batch_kernel<D2Q37, ST, COLL_BGK> : (void*)&launch_step<D2Q37, ST, COLL_BGK>;
+    return nullptr;
+}
+
+// Plain step with diffuse-scattering walls.
+template <class ST>
+void* q37_plain_ds(int coll) {
+    if (coll == COLL_REG) return (void*)&launch_step<D2Q37, ST, COLL_REG, 1>;
+    if (coll == COLL_BGK) return (void*)&launch_step<D2Q37, ST, COLL_BGK, 1>;
+    return nullptr;
+}
+
+// Plain step with an occupancy floor: variant 1 = 6, 2 = 7 blocks of 128 threads per SM; 3, 4 = 7
+// blocks, each thread computing 2 or 4 nodes of its column (tiles of 32 x 8, 32 x 16 nodes).
+template <class ST, int COLL>
+void* q37_occ_c(int variant) {
+    switch (variant) {
+        case 1: return (void*)&launch_step_occ<D2Q37, ST, COLL, 6>;
+        case 2: return (void*)&launch_step_occ<D2Q37, ST, COLL, 7>;
+        case 3: return (void*)&launch_step_occn<D2Q37, ST, COLL, 7, 2>;
+        case 4: return (void*)&launch_step_occn<D2Q37, ST, COLL, 7, 4>;
+        default: return nullptr;
+    }
+}
+
+// Staged steps (tiles in nodes): 10, 11, 12 = one node per thread on 32 x 4, 64 x 2, 64 x 4 tiles;
+// 13 = 64 x 2 with the outputs stored through TMA; 18, 23, 24, 25 = several nodes per thread, one
+// row apart: blocks of 64 x 1 (4 rows), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks per SM),
+// 128 x 1 (2 rows) threads.
+template <class ST, int COLL>
+void* q37_tma_c(int variant) {
+    switch (variant) {
+        case 10: return (void*)&launch_step_tma1<D2Q37, ST, COLL, 32, 4>;
+        case 11: return (void*)&launch_step_tma1<D2Q37, ST, COLL, 64, 2>;
+        case 12: return (void*)&launch_step_tma1<D2Q37, ST, COLL, 64, 4>;
+        case 13: return (void*)&launch_step_tma1s<D2Q37, ST, COLL, 64, 2>;
+        case 18: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 4, 12>;
+        case 23: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 2, 12>;
+        case 24: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 4, 10>;
+        case 25: return (void*)&launch_step_tman<D2Q37, ST, COLL, 128, 1, 2, 6>;
+        default: return nullptr;
+    }
+}
+
+template <class ST>
+void* q37_occ(int coll, int variant) {
+    return coll == COLL_REG ? q37_occ_c<ST, COLL_REG>(variant) : coll == COLL_BGK ? q37_occ_c<ST, COLL_BGK>(variant)
+                                                                                    : nullptr;
+}
+
+template <class ST>
+void* q37_tma(int coll, int variant) {
+    return coll == COLL_REG ? q37_tma_c<ST, COLL_REG>(variant) : coll == COLL_BGK ? q37_tma_c<ST, COLL_BGK>(variant)
+                                                                                    : nullptr;
+}
+
+// Box of the staged kernels for tile width bx: width (elements) and left pad.
+template <class ST>
+void q37_box(int bx, int* bw, int* pad) {
+    *pad = TmaGeom<D2Q37, ST, 1>::PAD;
+    *bw = bx + 2 * *pad;
+}
+
+}  // namespace lbm
+
+// The functions one translation unit exports for storage type ST under the suffix SFX.
+#define LBM_Q37_EXPORTS(SFX, ST, STAGED)                                                                 \
+    namespace lbm {                                                                                      \
+    void* find_launcher_q37_##SFX(int coll, bool batched) { return q37_plain<ST>(coll, batched); }     \
+    void* find_launcher_q37_##SFX##_ds(int coll) { return q37_plain_ds<ST>(coll); }                    \
+    void* find_occ_launcher_q37_##SFX(int coll, int variant) {                                          \
+        return STAGED ? q37_occ<ST>(coll, variant) : nullptr;                                            \
+    }                                                                                                    \
+    void* find_tma_launcher_q37_##SFX(int coll, int variant) {                                          \
+        return STAGED ? q37_tma<ST>(coll, variant) : nullptr;                                            \
+    }                                                                                                    \
+    void tma_box_q37_##SFX(int bx, int* bw, int* pad) {                                                 \
+        if (STAGED) q37_box<ST>(bx, bw, pad);                                                            \
+        else *bw = *pad = 0;                                                                             \
+    }                                                                                                    \
+    }

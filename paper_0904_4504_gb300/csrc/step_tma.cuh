@@ -252,6 +252,58 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1(const __grid_constan
     tile_epilogue(P, t, P.force_out, Fx, Fy);
 }
 
+// Single-instance step, one block per tile of BX x (NR BY) nodes: the tile is staged by one set of
+// Q bulk copies, and each thread computes NR nodes of its column, one row of BY apart at a time.
+// The block's fixed costs (tile indices, launch constants, the copies and their barrier, the
+// force epilogue) are spread over NR nodes per thread, while only one node's populations are live.
+// MINB: resident blocks per SM the register allocation must allow (the compiler would otherwise keep
+// launch constants live across the rows at the price of occupancy).
+template <class L, class ST, int COLL, int BX, int BY, int NR, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_constant__ InstDev P,
+                                                            const __grid_constant__ CUtensorMap map) {
+    using G = TmaGeom<L, ST, 1, BX, BY * NR>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
+    const int t = blockIdx.x;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int x = (t % P.ntx) * BX + threadIdx.x;
+    const int yt = (t / P.ntx) * (BY * NR);
+    const bool interior = tile_interior<G, L>(P, t);
+    if (interior) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tile<G, L>(P, &map, t, smem, &bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(&bar, 0, kTmaWaitLimit);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(P.err, 4);
+                mbar_wait(&bar, 0, kTmaWaitLimit);
+            }
+            __syncthreads();
+            return;
+        }
+    }
+    double Fx = 0.0, Fy = 0.0;
+#pragma unroll 1
+    for (int r = 0; r < NR; ++r) {
+        const int ty = threadIdx.y + r * BY;
+        const int y = yt + ty;
+        const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+        if (cls == NODE_SOLID) continue;
+        typename StoreT<ST>::CT h[L::Q];
+        if (interior)
+            gather_smem<G, L, ST>(smem, threadIdx.x, ty, h);
+        else
+            gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
+        collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, h, Fx, Fy);
+    }
+    tile_epilogue(P, t, P.force_out, Fx, Fy);
+}
+
 // Eq. 17 from a staged tile for the two neighbouring nodes (2 tx, 2 tx + 1) of a thread; a
 // direction with even c_ix has both values in one aligned two-element word.
 template <class G, class L, class ST>
@@ -367,6 +419,20 @@ cudaError_t launch_step_tma1(const InstDev& P, const CUtensorMap& map, const CUt
     return launch_pdl(step_kernel_tma1<L, ST, COLL, BX, BY>, dim3(P.ntiles), dim3(BX, BY), G::SMEM, stream, P, map);
 }
 
+template <class L, class ST, int COLL, int BX, int BY, int NR, int MINB>
+cudaError_t launch_step_tman(const InstDev& P, const CUtensorMap& map, const CUtensorMap&, cudaStream_t stream) {
+    using G = TmaGeom<L, ST, 1, BX, BY * NR>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel_tman<L, ST, COLL, BX, BY, NR, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(step_kernel_tman<L, ST, COLL, BX, BY, NR, MINB>, dim3(P.ntiles), dim3(BX, BY), G::SMEM, stream,
+                      P, map);
+}
+
 // The staged step with staged stores: an interior tile's outputs are written to a second
 // shared-memory tile at compile-time offsets, then one thread stores each direction plane with one
 // bulk tensor copy (box BX x BY at the tile's origin, never negative, x a multiple of BX) and waits
@@ -430,7 +496,9 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1s(const __grid_consta
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) tma_store_3d(&smap, x0, y0, i, out + i * O::OSLOT);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            // the block may exit once the copies have read its shared memory; the global writes
+            // complete with the grid
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
     } else if (cls != NODE_SOLID) {
         gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
