@@ -470,8 +470,82 @@ __device__ __forceinline__ void eval_pair(const Coef<T>& C, int k, T hp, T hm, T
     }
 }
 
+// Two FP32 lanes in one 64-bit register pair, and the packed FP32 operations of sm_100+ (each lane
+// rounds to nearest like the scalar operation; one instruction issues both).
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(F2 a, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+
+// Outputs of the pairs k and k + 1 of the regularized collision in FP32, two pairs per packed
+// operation.  The pair tables list pairs in groups of two that share their arithmetic: (p_x, p_y)
+// and (p_x, -p_y), or (m, 0) and (0, m).  Same expressions as eval_pair, evaluated in a different
+// order (FP32 rounding differs).
+template <class L>
+__device__ __forceinline__ void eval_group(const Coef<float>& C, int k, F2 E1, F2 E2, F2 O0, F2 O1, float& op1,
+                                           float& om1, float& op2, float& om2) {
+    const int px1 = L::px(k), py1 = L::py(k), px2 = L::px(k + 1), py2 = L::py(k + 1);
+    float a1, a2, q1, q2, k1, k2, c1, c2;
+    if (px1 == px2 && py1 == -py2) {
+        // (p_x, +-p_y): a = X +- Y, shared even constant, opposite mixed terms
+        const float X = (float)px1 * C.ax, Y = (float)py1 * C.ay;
+        a1 = X + Y;
+        a2 = X - Y;
+        const float B = C.ce[px1] + (float)(px1 * px1) * C.rxx + (float)(py1 * py1) * C.ryy;
+        q1 = B + (float)(px1 * py1) * C.rxy;
+        q2 = B - (float)(px1 * py1) * C.rxy;
+        k1 = k2 = (float)px1 * C.kf;
+        c1 = c2 = C.co[px1];
+    } else {
+        // (m, 0) and (0, m)
+        a1 = (float)px1 * C.ax + (float)py1 * C.ay;
+        a2 = (float)px2 * C.ax + (float)py2 * C.ay;
+        q1 = C.ce[px1] + (float)(px1 * px1) * C.rxx + (float)(py1 * py1) * C.ryy + (float)(px1 * py1) * C.rxy;
+        q2 = C.ce[px2] + (float)(px2 * px2) * C.rxx + (float)(py2 * py2) * C.ryy + (float)(px2 * py2) * C.rxy;
+        k1 = (float)px1 * C.kf;
+        k2 = (float)px2 * C.kf;
+        c1 = C.co[px1];
+        c2 = C.co[px2];
+    }
+    const F2 A = f2(a1, a2);
+    const F2 A2 = mul2(A, A);
+    F2 E = fma2(A2, fma2(A2, E2, E1), f2(q1, q2));
+    E = fma2(A, f2(k1, k2), E);
+    const F2 O = fma2(A, fma2(O1, A2, O0), f2(c1, c2));
+    f2_split(add2(E, O), op1, op2);
+    f2_split(sub2(E, O), om1, om2);
+}
+
 // prepare + evaluation of one node; emit(i, v) receives output i in storage units (relative to the
-// stream offset when it is on).
+// stream offset when it is on).  The regularized collision in FP32 evaluates two pairs per packed
+// operation.
 template <class L, class ST, int COLL, int WALL = 0, class Emit>
 __device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                              float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
@@ -480,12 +554,25 @@ __device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v
     Coef<T> C;
     prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
     emit(0, eval_rest<L, COLL, T>(C, h[0]));
+    if constexpr (COLL == COLL_REG && sizeof(T) == 4 && L::NP % 2 == 0) {
+        const F2 E1 = f2(C.e1, C.e1), E2 = f2(C.e2, C.e2), O0 = f2(C.o0, C.o0), O1 = f2(C.o1, C.o1);
 #pragma unroll
-    for (int k = 0; k < L::NP; ++k) {
-        T op, omn;
-        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        emit(1 + 2 * k, op);
-        emit(2 + 2 * k, omn);
+        for (int k = 0; k < L::NP; k += 2) {
+            float op1, om1, op2, om2;
+            eval_group<L>(C, k, E1, E2, O0, O1, op1, om1, op2, om2);
+            emit(1 + 2 * k, op1);
+            emit(2 + 2 * k, om1);
+            emit(3 + 2 * k, op2);
+            emit(4 + 2 * k, om2);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::NP; ++k) {
+            T op, omn;
+            eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
+            emit(1 + 2 * k, op);
+            emit(2 + 2 * k, omn);
+        }
     }
 }
 
