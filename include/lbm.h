@@ -189,8 +189,9 @@ int lbm_set_tile(lbm_sim* sim, int block_x, int block_y);
  * 10, 11, 12: one node per thread, one block per tile of 32 x 4, 64 x 2 or 64 x 4 nodes;
  * 13: as 11, with the outputs of interior tiles staged in shared memory and written by one bulk
  * tensor store per direction plane (D2Q37);
- * 18, 23, 24, 25: several nodes per thread, one row apart, on blocks of 64 x 1 (4 rows, at least 12
- * blocks per SM), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks), 128 x 1 (2 rows) threads (D2Q37);
+ * 18, 23, 24, 25, 26, 27: several nodes per thread, one row apart, on blocks of 64 x 1 (4 rows, at
+ * least 12 blocks per SM), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks), 128 x 1 (2 rows), 64 x 1
+ * (3 rows, 12 blocks), 64 x 1 (3 rows, 11 blocks) threads (D2Q37);
  * 20: two neighbouring nodes per thread with paired loads and stores, 64 x 4 tiles (D2Q9).
  * Every variant evaluates the same expressions in the same order; results agree to FP32 rounding
  * (the compiler may contract them into different fused multiply-adds in different kernels) and the
@@ -302,7 +303,7 @@ int lbm_batch_remove(lbm_batch* batch, int slot);
 int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
- * numbers; -1, the default: for D2Q37 the staged variant 24 with 16-bit storage and variant 2 with
+ * numbers; -1, the default: for D2Q37 the staged variant 26 with 16-bit storage and variant 2 with
  * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
  * support falls back to the plain kernel.  Ignored by the persistent mode.  LBM_EINVAL for a number
  * below -1. */

@@ -78,6 +78,8 @@ static bool variant_tile(int variant, int* bx, int* by) {
         case 23: *bx = 64; *by = 2; return true;
         case 24: *bx = 64; *by = 4; return true;
         case 25: *bx = 128; *by = 2; return true;
+        case 26:
+        case 27: *bx = 64; *by = 3; return true;
         case 20: *bx = 64; *by = 4; return true;
         case 21: *bx = 64; *by = 2; return true;
         case 22: *bx = 128; *by = 2; return true;
@@ -1060,7 +1062,7 @@ int lbm_tune(lbm_sim* s, int steps, lbm_tune_entry* out, int cap, int* n_out) {
     if (steps < 1 || !n_out || (cap > 0 && !out)) return set_error(LBM_EINVAL, "need steps >= 1 and an output");
     // candidates: plain kernel tiles, then every staged variant built for this storage type
     const int tiles[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {32, 2}};
-    const int variants[] = {1, 2, 3, 4, 10, 11, 12, 13, 18, 20, 23, 24, 25};
+    const int variants[] = {1, 2, 3, 4, 10, 11, 12, 13, 18, 20, 23, 24, 25, 26, 27};
     std::vector<lbm_tune_entry> cand;
     for (auto& t : tiles) cand.push_back(lbm_tune_entry{0, t[0], t[1], 0.0});
     for (int v : variants)

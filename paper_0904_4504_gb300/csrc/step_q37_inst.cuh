@@ -41,7 +41,7 @@ void* q37_occ_c(int variant) {
 // Staged steps (tiles in nodes): 10, 11, 12 = one node per thread on 32 x 4, 64 x 2, 64 x 4 tiles;
 // 13 = 64 x 2 with the outputs stored through TMA; 18, 23, 24, 25 = several nodes per thread, one
 // row apart: blocks of 64 x 1 (4 rows), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks per SM),
-// 128 x 1 (2 rows) threads.
+// 128 x 1 (2 rows) threads; 26, 27 = 64 x 1 threads, 3 rows, at least 12 or 11 blocks per SM.
 template <class ST, int COLL>
 void* q37_tma_c(int variant) {
     switch (variant) {
@@ -53,6 +53,8 @@ void* q37_tma_c(int variant) {
         case 23: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 2, 12>;
         case 24: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 4, 10>;
         case 25: return (void*)&launch_step_tman<D2Q37, ST, COLL, 128, 1, 2, 6>;
+        case 26: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 3, 12>;
+        case 27: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 3, 11>;
         default: return nullptr;
     }
 }

@@ -209,7 +209,7 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
     configs = [("tile", (32, 8)), ("tile", (64, 4)), ("tile", (128, 1)), ("tile", (32, 16)),
                ("variant", 1), ("variant", 2), ("variant", 3), ("variant", 4), ("variant", 10), ("variant", 11),
                ("variant", 12), ("variant", 13),
-               ("variant", 18), ("variant", 23), ("variant", 24), ("variant", 25)]
+               ("variant", 18), ("variant", 23), ("variant", 24), ("variant", 25), ("variant", 26), ("variant", 27)]
     for kind, arg in configs:
         geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
                                storage=storage)
@@ -235,7 +235,7 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
         assert np.abs(F - outs[0][1]).max() <= Ftol, (kind, arg)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 10, 11, 12, 13, 18, 23, 24, 25])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 10, 11, 12, 13, 18, 23, 24, 25, 26, 27])
 def test_parity_staged_variants(variant):
     """The occupancy-floor (1, 2) and TMA-staged kernels against the oracle on a grid with interior
     tiles, FP32."""
