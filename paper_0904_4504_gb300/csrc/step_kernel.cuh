@@ -670,6 +670,24 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double
     tile_epilogue_n<1>(P, tile, force_out, F);
 }
 
+// Node (x, y) inside the grid.  With 4- and 8-byte storage its class and its pulled populations
+// are loaded together (the pulls of any node inside the grid are in bounds, so they need not wait
+// for the class), then a fluid node collides and stores; solid nodes load for nothing, a small
+// fraction of a grid.  The 16-bit kernels run at a register budget where holding the class
+// through the loads spills, so they read the class first.
+template <class L, class ST, int COLL, int WALL = 0>
+__device__ __forceinline__ void node_update_inside(const InstDev& P, const void* src, void* dst, int x, int y,
+                                                   double dv, float dv_f, double& Fx, double& Fy) {
+    const int cls = (int)P.cls[y * P.pitch + x];
+    if constexpr (sizeof(ST) == 2) {
+        if (cls != NODE_SOLID) node_update<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
+    } else {
+        typename StoreT<ST>::CT h[L::Q];
+        gather_global<L, ST>(P, static_cast<const ST*>(src), x, y, h);
+        if (cls != NODE_SOLID) collide_store<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, h, Fx, Fy);
+    }
+}
+
 // One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
 template <class L, class ST, int COLL, int WALL = 0>
 __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const void* src, void* dst, double dv,
@@ -678,8 +696,7 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
     double Fx = 0.0, Fy = 0.0;
-    const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-    if (cls != NODE_SOLID) node_update<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
+    if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, WALL>(P, src, dst, x, y, dv, dv_f, Fx, Fy);
     tile_epilogue(P, tile, force_out, Fx, Fy);
 }
 
@@ -798,8 +815,7 @@ __global__ void __launch_bounds__(128, MINB) step_kernel_occn(const __grid_const
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
         const int y = y0 + 4 * r;
-        const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-        if (cls != NODE_SOLID) node_update<L, ST, COLL, 0>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, Fx, Fy);
+        if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, 0>(P, P.src, P.dst, x, y, P.dv, P.dv_f, Fx, Fy);
     }
     tile_epilogue(P, t, P.force_out, Fx, Fy);
 }

@@ -270,6 +270,13 @@ __global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_c
     const int x = (t % P.ntx) * BX + threadIdx.x;
     const int yt = (t / P.ntx) * (BY * NR);
     const bool interior = tile_interior<G, L>(P, t);
+    // classes of this thread's nodes, fetched while the tile's copies fly
+    int cls[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int y = yt + threadIdx.y + r * BY;
+        cls[r] = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+    }
     if (interior) {
         if (tid == 0) {
             mbar_init(&bar, 1);
@@ -292,14 +299,16 @@ __global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_c
     for (int r = 0; r < NR; ++r) {
         const int ty = threadIdx.y + r * BY;
         const int y = yt + ty;
-        const int cls = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
-        if (cls == NODE_SOLID) continue;
+        const int c = cls[0];
+#pragma unroll
+        for (int j = 0; j + 1 < NR; ++j) cls[j] = cls[j + 1];  // rotate: stays in registers
+        if (c == NODE_SOLID) continue;
         typename StoreT<ST>::CT h[L::Q];
         if (interior)
             gather_smem<G, L, ST>(smem, threadIdx.x, ty, h);
         else
             gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
-        collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, h, Fx, Fy);
+        collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, c, P.dv, P.dv_f, h, Fx, Fy);
     }
     tile_epilogue(P, t, P.force_out, Fx, Fy);
 }
