@@ -152,6 +152,7 @@ template <class L, class ST, int COLL, int PHASE>
 __global__ void __launch_bounds__(512) step_kernel_aa(const __grid_constant__ InstDev P) {
     pdl_wait_then_release();
     const int tile = blockIdx.x;
+    const int slot = P.tile_slot[tile];
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(512) step_kernel_aa(const __grid_constant__ In
     if (PHASE == 0) {
         double F[4] = {0.0, 0.0, 0.0, 0.0};
         if (cls != NODE_SOLID) aa_pull_push<L, ST, COLL>(P, A, x, y, cls, F[0], F[1], F[2], F[3]);
-        tile_epilogue_n<2>(P, tile, P.force_out, F);
+        tile_epilogue_n<2>(P, slot, P.force_out, F);
     } else if (cls != NODE_SOLID) {
         aa_local<L, ST, COLL>(P, A, x, y, cls);
     }

@@ -605,8 +605,7 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src, v
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
 // the slots in a fixed order, adds the constant part and writes the force of the step.
 template <int NF>
-__device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int tile, double2* force_out, double (&F)[2 * NF]) {
-    const int slot = P.tile_slot[tile];
+__device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int slot, double2* force_out, double (&F)[2 * NF]) {
     if (slot < 0) return;  // block-uniform: no body link in this tile
     __shared__ double2 red[32 * NF];
     __shared__ int last;
@@ -665,9 +664,9 @@ __device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int tile, doub
     }
 }
 
-__device__ __forceinline__ void tile_epilogue(const InstDev& P, int tile, double2* force_out, double Fx, double Fy) {
+__device__ __forceinline__ void tile_epilogue(const InstDev& P, int slot, double2* force_out, double Fx, double Fy) {
     double F[2] = {Fx, Fy};
-    tile_epilogue_n<1>(P, tile, force_out, F);
+    tile_epilogue_n<1>(P, slot, force_out, F);
 }
 
 // Node (x, y) inside the grid.  With 4- and 8-byte storage its class and its pulled populations
@@ -695,9 +694,13 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
     const int tx = tile % P.ntx, ty = tile / P.ntx;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
+    // 16-bit kernels read their tile's slot early, so that the epilogue need not wait for it; the
+    // 4- and 8-byte kernels have no register left for it (it spilled) and read it at the end
+    int slot = sizeof(ST) == 2 ? P.tile_slot[tile] : 0;
     double Fx = 0.0, Fy = 0.0;
     if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, WALL>(P, src, dst, x, y, dv, dv_f, Fx, Fy);
-    tile_epilogue(P, tile, force_out, Fx, Fy);
+    if (sizeof(ST) != 2) slot = P.tile_slot[tile];
+    tile_epilogue(P, slot, force_out, Fx, Fy);
 }
 
 // Single-instance step: one block per tile.
@@ -811,13 +814,14 @@ __global__ void __launch_bounds__(128, MINB) step_kernel_occn(const __grid_const
     const int t = blockIdx.x;
     const int x = (t % P.ntx) * 32 + threadIdx.x;
     const int y0 = (t / P.ntx) * (4 * NR) + threadIdx.y;
+    const int slot = P.tile_slot[t];
     double Fx = 0.0, Fy = 0.0;
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
         const int y = y0 + 4 * r;
         if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, 0>(P, P.src, P.dst, x, y, P.dv, P.dv_f, Fx, Fy);
     }
-    tile_epilogue(P, t, P.force_out, Fx, Fy);
+    tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
 template <class L, class ST, int COLL, int MINB, int NR>

@@ -171,7 +171,7 @@ __device__ __forceinline__ bool run_tiles_tma(const InstDev& P, const CUtensorMa
             gather_global<L, ST>(P, static_cast<const ST*>(src), x, y, h);
             collide_store<L, ST, COLL>(P, src, dst, x, y, cls, dv, dv_f, h, Fx, Fy);
         }
-        tile_epilogue(P, t, force_out, Fx, Fy);
+        tile_epilogue(P, P.tile_slot[t], force_out, Fx, Fy);
         __syncthreads();  // stage s may be refilled now
     }
     if (!ok_all) {
@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1(const __grid_constan
     __shared__ __align__(8) uint64_t bar;
     pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
+    const int slot = P.tile_slot[t];  // read early: the epilogue would otherwise wait for it
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int x = (t % P.ntx) * BX + threadIdx.x;
     const int y = (t / P.ntx) * BY + threadIdx.y;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1(const __grid_constan
         gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
         collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, h, Fx, Fy);
     }
-    tile_epilogue(P, t, P.force_out, Fx, Fy);
+    tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
 // Single-instance step, one block per tile of BX x (NR BY) nodes: the tile is staged by one set of
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_c
     __shared__ __align__(8) uint64_t bar;
     pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
+    const int slot = P.tile_slot[t];  // read early: the epilogue would otherwise wait for it
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int x = (t % P.ntx) * BX + threadIdx.x;
     const int yt = (t / P.ntx) * (BY * NR);
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_c
             gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
         collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, c, P.dv, P.dv_f, h, Fx, Fy);
     }
-    tile_epilogue(P, t, P.force_out, Fx, Fy);
+    tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
 // Eq. 17 from a staged tile for the two neighbouring nodes (2 tx, 2 tx + 1) of a thread; a
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
     __shared__ __align__(8) uint64_t bar;
     pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
+    const int slot = P.tile_slot[t];  // read early: the epilogue would otherwise wait for it
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int x = (t % P.ntx) * (2 * TX) + 2 * threadIdx.x;
     const int y = (t / P.ntx) * TY + threadIdx.y;
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_pair(const __grid_constan
             S::st2(dst + (2 + 2 * k) * plane, m0, m1);
         }
     }
-    tile_epilogue(P, t, P.force_out, Fx, Fy);
+    tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
 template <class L, class ST, int COLL, int TX, int TY>
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1s(const __grid_consta
     __shared__ __align__(8) uint64_t bar;
     pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     const int t = blockIdx.x;
+    const int slot = P.tile_slot[t];  // read early: the epilogue would otherwise wait for it
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int x = (t % P.ntx) * BX + threadIdx.x;
     const int y = (t / P.ntx) * BY + threadIdx.y;
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel_tma1s(const __grid_consta
         gather_global<L, ST>(P, static_cast<const ST*>(P.src), x, y, h);
         collide_store<L, ST, COLL>(P, P.src, P.dst, x, y, cls, P.dv, P.dv_f, h, Fx, Fy);
     }
-    tile_epilogue(P, t, P.force_out, Fx, Fy);
+    tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
 template <class L, class ST, int COLL, int BX, int BY>
