@@ -669,15 +669,14 @@ __device__ __forceinline__ void tile_epilogue(const InstDev& P, int slot, double
     tile_epilogue_n<1>(P, slot, force_out, F);
 }
 
-// Node (x, y) inside the grid.  With 4- and 8-byte storage its class and its pulled populations
-// are loaded together (the pulls of any node inside the grid are in bounds, so they need not wait
-// for the class), then a fluid node collides and stores; solid nodes load for nothing, a small
-// fraction of a grid.  The 16-bit kernels run at a register budget where holding the class
-// through the loads spills, so they read the class first.
+// Node (x, y) inside the grid, of class cls (already loaded).  With 4- and 8-byte storage its pulls
+// are issued whatever the class (the pulls of any node inside the grid are in bounds, so they need
+// not wait for the class test), then a fluid node collides and stores; solid nodes load for
+// nothing, a small fraction of a grid.  The 16-bit kernels run at a register budget where that
+// spills, so they test the class first.
 template <class L, class ST, int COLL, int WALL = 0>
-__device__ __forceinline__ void node_update_inside(const InstDev& P, const void* src, void* dst, int x, int y,
-                                                   double dv, float dv_f, double& Fx, double& Fy) {
-    const int cls = (int)P.cls[y * P.pitch + x];
+__device__ __forceinline__ void node_update_cls(const InstDev& P, const void* src, void* dst, int x, int y, int cls,
+                                                double dv, float dv_f, double& Fx, double& Fy) {
     if constexpr (sizeof(ST) == 2) {
         if (cls != NODE_SOLID) node_update<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
     } else {
@@ -687,8 +686,10 @@ __device__ __forceinline__ void node_update_inside(const InstDev& P, const void*
     }
 }
 
-// One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.
-template <class L, class ST, int COLL, int WALL = 0>
+// One tile of one instance: blockDim.x * blockDim.y nodes, one thread per node.  PDL: the kernel
+// was launched with programmatic stream serialization; the node's class (geometry, written by the
+// host only) is read before the wait for the previous step's grid, the populations after it.
+template <class L, class ST, int COLL, int WALL = 0, bool PDL = false>
 __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const void* src, void* dst, double dv,
                                              float dv_f, double2* force_out) {
     const int tx = tile % P.ntx, ty = tile / P.ntx;
@@ -697,8 +698,11 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
     // 16-bit kernels read their tile's slot early, so that the epilogue need not wait for it; the
     // 4- and 8-byte kernels have no register left for it (it spilled) and read it at the end
     int slot = sizeof(ST) == 2 ? P.tile_slot[tile] : 0;
+    const bool inside = x < P.nx && y < P.ny;
+    const int cls = inside ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
+    if (PDL) pdl_wait_then_release();
     double Fx = 0.0, Fy = 0.0;
-    if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, WALL>(P, src, dst, x, y, dv, dv_f, Fx, Fy);
+    if (inside) node_update_cls<L, ST, COLL, WALL>(P, src, dst, x, y, cls, dv, dv_f, Fx, Fy);
     if (sizeof(ST) != 2) slot = P.tile_slot[tile];
     tile_epilogue(P, slot, force_out, Fx, Fy);
 }
@@ -706,8 +710,7 @@ __device__ __forceinline__ void process_tile(const InstDev& P, int tile, const v
 // Single-instance step: one block per tile.
 template <class L, class ST, int COLL, int WALL = 0>
 __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstDev P) {
-    pdl_wait_then_release();
-    process_tile<L, ST, COLL, WALL>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
+    process_tile<L, ST, COLL, WALL, true>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
 // One instance of a batch: its step-kernel parameters plus what changes from step to step.
@@ -796,8 +799,7 @@ cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
 // kernel waits on its global loads; more resident warps hide more of that latency.
 template <class L, class ST, int COLL, int MINB>
 __global__ void __launch_bounds__(128, MINB) step_kernel_occ(const __grid_constant__ InstDev P) {
-    pdl_wait_then_release();
-    process_tile<L, ST, COLL, 0>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
+    process_tile<L, ST, COLL, 0, true>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
 template <class L, class ST, int COLL, int MINB>
@@ -819,7 +821,8 @@ __global__ void __launch_bounds__(128, MINB) step_kernel_occn(const __grid_const
 #pragma unroll 1
     for (int r = 0; r < NR; ++r) {
         const int y = y0 + 4 * r;
-        if (x < P.nx && y < P.ny) node_update_inside<L, ST, COLL, 0>(P, P.src, P.dst, x, y, P.dv, P.dv_f, Fx, Fy);
+        if (x < P.nx && y < P.ny)
+            node_update_cls<L, ST, COLL, 0>(P, P.src, P.dst, x, y, (int)P.cls[y * P.pitch + x], P.dv, P.dv_f, Fx, Fy);
     }
     tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }

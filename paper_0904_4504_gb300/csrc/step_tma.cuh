@@ -265,26 +265,27 @@ __global__ void __launch_bounds__(BX * BY, MINB) step_kernel_tman(const __grid_c
     using G = TmaGeom<L, ST, 1, BX, BY * NR>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
-    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
+    // The geometry (tile slots, node classes) is written by the host only: it is read before the
+    // wait for the previous step's grid, while that grid drains.
     const int t = blockIdx.x;
     const int slot = P.tile_slot[t];  // read early: the epilogue would otherwise wait for it
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int x = (t % P.ntx) * BX + threadIdx.x;
     const int yt = (t / P.ntx) * (BY * NR);
     const bool interior = tile_interior<G, L>(P, t);
-    // classes of this thread's nodes, fetched while the tile's copies fly
     int cls[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int y = yt + threadIdx.y + r * BY;
         cls[r] = (x < P.nx && y < P.ny) ? (int)P.cls[y * P.pitch + x] : (int)NODE_SOLID;
     }
+    if (interior && tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    pdl_wait_then_release();  // before the tile's copies: they read the previous step's output
     if (interior) {
-        if (tid == 0) {
-            mbar_init(&bar, 1);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tile<G, L>(P, &map, t, smem, &bar);
-        }
+        if (tid == 0) issue_tile<G, L>(P, &map, t, smem, &bar);
         __syncthreads();
         const bool ok = mbar_wait(&bar, 0, kTmaWaitLimit);
         if (!__syncthreads_and(ok)) {
