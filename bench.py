@@ -501,7 +501,7 @@ def run_ours(args):
         if rank == 0:
             extras["batched_mixed_precision"] = {
                 "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024), "
-                            "streams mode (one launch of the staged step kernel per instance per step, on 8 "
+                            "streams mode (one launch of the staged step kernel per instance per step, on 16 "
                             "parallel streams), FP16 storage scaled by U0, FP32 arithmetic, FP64 force",
                 "value": bl["value"], "unit": "MLUPS", "steps": bl["steps"], "ms_per_step": bl["ms_per_step"],
                 "roofline": bl["roofline"], "clocks": bl["clocks"], "gpu_launches": bl["gpu_launches"],

@@ -34,7 +34,7 @@ constexpr long long kDefaultBarrierLimit = 4000000000ll;  // clock cycles (about
 
 }  // namespace
 
-constexpr int kSubStreams = 8;
+constexpr int kSubStreams = 16;
 
 struct lbm_batch {
     int device = 0, Q = 0, storage = 0, collision = 0;
