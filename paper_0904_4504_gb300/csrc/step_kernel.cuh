@@ -222,7 +222,7 @@ struct Coef {
     T ax, ay;                  // u / theta
     T c0, e1, e2, o0, o1;      // even part c0 + a^2 (e1 + a^2 e2), odd part a (o0 + o1 a^2)
     T rxx, rxy, ryy, hf;       // regularized part and first-order force part
-    T kf, inv_s;               // force coefficient, 1/s
+    T kf;                      // force coefficient
     T om, e0, kfu;             // plain BGK: 1/tau, equilibrium constant, even source constant
     // per m = |c_x| (0..3), with the stream offset of the stored state folded in (16-bit storage):
     // regularized: c0 - He[m] and m hf - Ho[m]; plain BGK: kfu - He[m] and m kf - Ho[m]
@@ -237,13 +237,175 @@ struct Coef {
 // when the populations were pushed (OWN_NONE: no fix-up here).
 enum OwnPlane { OWN_OPP = 0, OWN_SWAPPED = 1, OWN_NONE = 2 };
 
+// Eq. 16 on deviations: drho = sum g_i, j = sum g_i c_i, Pi' = sum g_i c_i c_i, in the units of
+// the populations (w_i divided out).  spdm(k, sp, dm) gives the sum and difference of pair k's two
+// populations, h0 the rest population.  The pair tables list pairs in groups of two of one shell:
+// (p_x, p_y) and (p_x, -p_y), whose sums S, D and differences Jp, Jm of sp and dm give the six
+// moments with one multiply-add each, or (m, 0) and (0, m), taken pair by pair.
+template <class L, class T, class SpDm>
+__device__ __forceinline__ void moments(SpDm&& spdm, T h0, T& m0, T& jx, T& jy, T& pxx, T& pxy, T& pyy) {
+    m0 = (T)L::w0() * h0;
+    jx = jy = pxx = pxy = pyy = (T)0;
+    auto one = [&](int k, T sp, T dm) {
+        const int px = L::px(k), py = L::py(k);
+        const double w = L::wp(k);
+        m0 += (T)w * sp;
+        if (px) jx += (T)(w * px) * dm;
+        if (py) jy += (T)(w * py) * dm;
+        if (px) pxx += (T)(w * px * px) * sp;
+        if (px && py) pxy += (T)(w * px * py) * sp;
+        if (py) pyy += (T)(w * py * py) * sp;
+    };
+#pragma unroll
+    for (int k = 0; k < L::NP; k += 2) {
+        T sp1, dm1;
+        spdm(k, sp1, dm1);
+        if (k + 1 == L::NP) {
+            one(k, sp1, dm1);
+            continue;
+        }
+        T sp2, dm2;
+        spdm(k + 1, sp2, dm2);
+        const int px = L::px(k), py = L::py(k);
+        if (px && py && L::px(k + 1) == px && L::py(k + 1) == -py && L::wp(k + 1) == L::wp(k)) {
+            const double w = L::wp(k);
+            const T S = sp1 + sp2, D = sp1 - sp2, Jp = dm1 + dm2, Jm = dm1 - dm2;
+            m0 += (T)w * S;
+            jx += (T)(w * px) * Jp;
+            jy += (T)(w * py) * Jm;
+            pxx += (T)(w * px * px) * S;
+            pxy += (T)(w * px * py) * D;
+            pyy += (T)(w * py * py) * S;
+        } else {
+            one(k, sp1, dm1);
+            one(k + 1, sp2, dm2);
+        }
+    }
+}
+
+// Collision coefficients of a node from its moments (storage units, relative to the stream offset
+// with 16-bit storage and the offset on): Eqs. 15 and 19 and the Guo-type source.  With 16-bit
+// storage the moments are scaled by s on the way in and the coefficients by 1/s on the way out.
+template <class L, class ST, int COLL>
+__device__ __forceinline__ void coef_tail(const InstDev& P, double dv, float dv_f, typename StoreT<ST>::CT m0,
+                                          typename StoreT<ST>::CT jx, typename StoreT<ST>::CT jy,
+                                          typename StoreT<ST>::CT pxx, typename StoreT<ST>::CT pxy,
+                                          typename StoreT<ST>::CT pyy, Coef<typename StoreT<ST>::CT>& C) {
+    using T = typename StoreT<ST>::CT;
+    constexpr bool SCALED = sizeof(ST) == 2;
+    if (SCALED) {
+        if (COLL == COLL_REG && P.stream_off) {
+            m0 += (T)P.HM[0]; jx += (T)P.HM[1]; jy += (T)P.HM[2];
+            pxx += (T)P.HM[3]; pxy += (T)P.HM[4]; pyy += (T)P.HM[5];
+        }
+        const T s = kconst<T>(P.s, P.s_f);
+        m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
+    }
+    constexpr double TH = L::theta();
+    const T th = (T)TH, ith = (T)(1.0 / TH);
+    const T drho = m0;
+    const T rho = kconst<T>(P.rho0, P.rho0_f) + drho;
+    const T irho = (T)1 / rho;
+    const T Fbx = P.body_force ? rho * kconst<T>(dv, dv_f) : (T)0;
+    const T ux = (jx + (T)0.5 * Fbx) * irho;
+    const T uy = jy * irho;
+    C.ax = ux * ith;
+    C.ay = uy * ith;
+    const T b = (ux * ux + uy * uy) * ith;
+
+    // Eq. 15 (+ 4th order): g_i^eq / w_i = E(a^2) + O(a), a = c_i.u/theta
+    T e0 = drho - (T)0.5 * rho * b, e1 = (T)0.5 * rho, e2 = 0, o0 = rho, o1 = 0;
+    if (P.eq_order >= 4) {
+        e0 += (T)0.125 * rho * b * b;
+        e1 -= (T)0.25 * rho * b;
+        e2 = rho * (T)(1.0 / 24.0);
+        o0 -= (T)0.5 * rho * b;
+        o1 = rho * (T)(1.0 / 6.0);
+    }
+    C.e1 = e1;
+    C.e2 = e2;
+    C.o0 = o0;
+    C.o1 = o1;
+    // Guo-type source, even part kf (a c_x - u_x) and odd part c_x * (kf or F/(2 theta))
+    const T kf = kconst<T>(P.src_k, P.src_k_f) * Fbx;
+    const T kfu = -kf * ux;
+    C.kf = kf;
+    if (COLL == COLL_REG) {
+        // Eq. 19: Pi^ne = Pi - Pi^eq with Pi^eq = rho theta I + rho u u (exact on these lattices)
+        const T Pxx = pxx - drho * th - rho * ux * ux;
+        const T Pxy = pxy - rho * ux * uy;
+        const T Pyy = pyy - drho * th - rho * uy * uy;
+        const T A = kconst<T>(P.reg_a, P.reg_a_f);
+        C.rxx = A * Pxx;
+        C.rxy = (T)2 * A * Pxy;
+        C.ryy = A * Pyy;
+        C.c0 = e0 - A * th * (Pxx + Pyy) + kfu;
+        C.hf = (T)0.5 * Fbx * ith;   // first-order part: kept J^ne = -F/2 plus the source
+    } else {
+        C.om = kconst<T>(P.omega_c, P.omega_c_f);
+        C.e0 = e0;
+        C.kfu = kfu;
+    }
+    if (SCALED) {
+        // outputs are wanted in storage units (divided by s): scale the coefficients once per node
+        const T is = kconst<T>(P.inv_s, P.inv_s_f);
+        C.c0 *= is; C.e1 *= is; C.e2 *= is; C.o0 *= is; C.o1 *= is;
+        C.rxx *= is; C.rxy *= is; C.ryy *= is; C.kf *= is; C.hf *= is;
+        C.e0 *= is; C.kfu *= is;
+    }
+    // constant parts of the outputs per m = |c_x|; 16-bit storage subtracts the stream offset of
+    // the stored state here, once per node (He, Ho are zero when it is off)
+    const T cbase = COLL == COLL_REG ? C.c0 : C.kfu, obase = COLL == COLL_REG ? C.hf : C.kf;
+#pragma unroll
+    for (int m = 0; m <= L::R; ++m) {
+        C.ce[m] = SCALED ? cbase - (T)P.He[m] : cbase;
+        C.co[m] = SCALED ? (T)m * obase - (T)P.Ho[m] : (T)m * obase;
+    }
+}
+
+// Eq. 12 on the blocked links of the boundary node at element offset idx: the node's own opposite
+// population comes back (from plane opp(i) of src, or plane i with OWN_SWAPPED), plus the moving-wall
+// term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out); adds the momentum the node's body links
+// hand to the body to (Fx, Fy).  With 16-bit storage and the stream offset on, h holds values
+// relative to the stream on entry and exit for the regularized collision, absolute ones for BGK.
+template <class L, class ST, int COLL, int OWN>
+__device__ __forceinline__ void bb_fixup(const InstDev& P, const ST* __restrict__ src, int idx, double dv,
+                                         typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy) {
+    using S = StoreT<ST>;
+    using T = typename S::CT;
+    const long long plane = P.plane;
+    const bool off = sizeof(ST) == 2 && P.stream_off;
+    const ulonglong2 lk = P.links[idx];
+    const unsigned long long blk = lk.x | lk.y;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        if ((blk >> i) & 1ull) {
+            const int cx = cx_of<L>(i), cy = cy_of<L>(i);
+            T own = S::ld(src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx);
+            if (off) own += (T)off_l<L>(P, opp_of<L>(i));
+            double mw = 0.0;
+            if ((lk.x >> i) & 1ull) {
+                if (P.moving) mw = P.mw_k * cx * dv;
+                // momentum c_opp h_opp in, c_i h_i^adv out: -c_i w_i s (h_opp + h_i^adv)
+                const double hs = 2.0 * (double)own + mw;
+                const double ws = w_of<L>(i) * P.s;
+                Fx -= cx * ws * hs;
+                Fy -= cy * ws * hs;
+            }
+            h[i] = own + (T)mw;
+            // the regularized path keeps h relative to the stream until the moments
+            if (off && COLL == COLL_REG) h[i] -= (T)off_l<L>(P, i);
+        }
+    }
+}
+
 template <class L, class ST, int COLL, int WALL = 0, int OWN = OWN_OPP>
 __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                         float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
                                         Coef<typename StoreT<ST>::CT>& C) {
     using S = StoreT<ST>;
     using T = typename S::CT;
-    constexpr int Q = L::Q, NP = L::NP;
+    constexpr int Q = L::Q;
     constexpr bool SCALED = sizeof(ST) == 2;
     const ST* __restrict__ src = static_cast<const ST*>(src_v);
     const long long plane = P.plane;
@@ -256,31 +418,8 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] += (T)off_l<L>(P, i);
     }
-    // Eq. 12 on blocked links: the node's own opposite population comes back, plus the
-    // moving-wall term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out)
     if (cls == NODE_BOUNDARY && WALL == 0 && OWN != OWN_NONE) {
-        const ulonglong2 lk = P.links[idx];
-        const unsigned long long blk = lk.x | lk.y;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if ((blk >> i) & 1ull) {
-                const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-                T own = S::ld(src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx);
-                if (off) own += (T)off_l<L>(P, opp_of<L>(i));
-                double mw = 0.0;
-                if ((lk.x >> i) & 1ull) {
-                    if (P.moving) mw = P.mw_k * cx * dv;
-                    // momentum c_opp h_opp in, c_i h_i^adv out: -c_i w_i s (h_opp + h_i^adv)
-                    const double hs = 2.0 * (double)own + mw;
-                    const double ws = w_of<L>(i) * P.s;
-                    Fx -= cx * ws * hs;
-                    Fy -= cy * ws * hs;
-                }
-                h[i] = own + (T)mw;
-                // the regularized path keeps h relative to the stream until the moments
-                if (off && COLL == COLL_REG) h[i] -= (T)off_l<L>(P, i);
-            }
-        }
+        bb_fixup<L, ST, COLL, OWN>(P, src, idx, dv, h, Fx, Fy);
     } else if (WALL == 1 && cls == NODE_BOUNDARY && OWN == OWN_OPP) {
         // Eq. 11 on blocked links: each wall returns its discrete Maxwellian at the wall velocity,
         // f_i = w_i rho_w (1 + e_i(U_w)), with rho_w set so that the node gets back exactly the mass
@@ -344,90 +483,12 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
         }
     }
 
-    // Eq. 16 on deviations: drho = sum g_i, j = sum g_i c_i, Pi' = sum g_i c_i c_i
-    T m0 = (T)L::w0() * h[0], jx = 0, jy = 0, pxx = 0, pxy = 0, pyy = 0;
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        const int px = L::px(k), py = L::py(k);
-        const double w = L::wp(k);
-        const T sp = h[1 + 2 * k] + h[2 + 2 * k];
-        const T dm = h[1 + 2 * k] - h[2 + 2 * k];
-        m0 += (T)w * sp;
-        if (px) jx += (T)(w * px) * dm;
-        if (py) jy += (T)(w * py) * dm;
-        if (px) pxx += (T)(w * px * px) * sp;
-        if (px && py) pxy += (T)(w * px * py) * sp;
-        if (py) pyy += (T)(w * py * py) * sp;
-    }
-    if (SCALED) {
-        if (off && COLL == COLL_REG) {
-            m0 += (T)P.HM[0]; jx += (T)P.HM[1]; jy += (T)P.HM[2];
-            pxx += (T)P.HM[3]; pxy += (T)P.HM[4]; pyy += (T)P.HM[5];
-        }
-        const T s = kconst<T>(P.s, P.s_f);
-        m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
-    }
-    constexpr double TH = L::theta();
-    const T th = (T)TH, ith = (T)(1.0 / TH);
-    const T drho = m0;
-    const T rho = kconst<T>(P.rho0, P.rho0_f) + drho;
-    const T irho = (T)1 / rho;
-    const T Fbx = P.body_force ? rho * kconst<T>(dv, dv_f) : (T)0;
-    const T ux = (jx + (T)0.5 * Fbx) * irho;
-    const T uy = jy * irho;
-    C.ax = ux * ith;
-    C.ay = uy * ith;
-    const T b = (ux * ux + uy * uy) * ith;
-
-    // Eq. 15 (+ 4th order): g_i^eq / w_i = E(a^2) + O(a), a = c_i.u/theta
-    T e0 = drho - (T)0.5 * rho * b, e1 = (T)0.5 * rho, e2 = 0, o0 = rho, o1 = 0;
-    if (P.eq_order >= 4) {
-        e0 += (T)0.125 * rho * b * b;
-        e1 -= (T)0.25 * rho * b;
-        e2 = rho * (T)(1.0 / 24.0);
-        o0 -= (T)0.5 * rho * b;
-        o1 = rho * (T)(1.0 / 6.0);
-    }
-    C.e1 = e1;
-    C.e2 = e2;
-    C.o0 = o0;
-    C.o1 = o1;
-    // Guo-type source, even part kf (a c_x - u_x) and odd part c_x * (kf or F/(2 theta))
-    const T kf = kconst<T>(P.src_k, P.src_k_f) * Fbx;
-    const T kfu = -kf * ux;
-    C.kf = kf;
-    C.inv_s = SCALED ? kconst<T>(P.inv_s, P.inv_s_f) : (T)1;
-    if (COLL == COLL_REG) {
-        // Eq. 19: Pi^ne = Pi - Pi^eq with Pi^eq = rho theta I + rho u u (exact on these lattices)
-        const T Pxx = pxx - drho * th - rho * ux * ux;
-        const T Pxy = pxy - rho * ux * uy;
-        const T Pyy = pyy - drho * th - rho * uy * uy;
-        const T A = kconst<T>(P.reg_a, P.reg_a_f);
-        C.rxx = A * Pxx;
-        C.rxy = (T)2 * A * Pxy;
-        C.ryy = A * Pyy;
-        C.c0 = e0 - A * th * (Pxx + Pyy) + kfu;
-        C.hf = (T)0.5 * Fbx * ith;   // first-order part: kept J^ne = -F/2 plus the source
-    } else {
-        C.om = kconst<T>(P.omega_c, P.omega_c_f);
-        C.e0 = e0;
-        C.kfu = kfu;
-    }
-    if (SCALED) {
-        // outputs are wanted in storage units (divided by s): scale the coefficients once per node
-        const T is = C.inv_s;
-        C.c0 *= is; C.e1 *= is; C.e2 *= is; C.o0 *= is; C.o1 *= is;
-        C.rxx *= is; C.rxy *= is; C.ryy *= is; C.kf *= is; C.hf *= is;
-        C.e0 *= is; C.kfu *= is;
-    }
-    // constant parts of the outputs per m = |c_x|; 16-bit storage subtracts the stream offset of
-    // the stored state here, once per node (He, Ho are zero when it is off)
-    const T cbase = COLL == COLL_REG ? C.c0 : C.kfu, obase = COLL == COLL_REG ? C.hf : C.kf;
-#pragma unroll
-    for (int m = 0; m <= L::R; ++m) {
-        C.ce[m] = SCALED ? cbase - (T)P.He[m] : cbase;
-        C.co[m] = SCALED ? (T)m * obase - (T)P.Ho[m] : (T)m * obase;
-    }
+    T m0, jx, jy, pxx, pxy, pyy;
+    moments<L, T>([&](int k, T& sp, T& dm) {
+        sp = h[1 + 2 * k] + h[2 + 2 * k];
+        dm = h[1 + 2 * k] - h[2 + 2 * k];
+    }, h[0], m0, jx, jy, pxx, pxy, pyy);
+    coef_tail<L, ST, COLL>(P, dv, dv_f, m0, jx, jy, pxx, pxy, pyy, C);
 }
 
 // Output of the rest direction, in storage units (the coefficients already carry 1/s).
@@ -543,17 +604,18 @@ __device__ __forceinline__ void eval_group(const Coef<float>& C, int k, F2 E1, F
     f2_split(sub2(E, O), om1, om2);
 }
 
-// prepare + evaluation of one node; emit(i, v) receives output i in storage units (relative to the
-// stream offset when it is on).  The regularized collision in FP32 evaluates two pairs per packed
-// operation.
-template <class L, class ST, int COLL, int WALL = 0, class Emit>
-__device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
-                                             float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
-                                             Emit&& emit) {
+// Evaluation of one node's outputs from its coefficients; emit(i, v) receives output i in storage
+// units (relative to the stream offset when it is on).  The regularized collision in FP32
+// evaluates two pairs per packed operation and never reads h; plain BGK reads the pulled h.
+template <class L, class ST, int COLL, class Emit>
+__device__ __forceinline__ void emit_outputs(const Coef<typename StoreT<ST>::CT>& C,
+                                             const typename StoreT<ST>::CT (&h)[L::Q], Emit&& emit) {
     using T = typename StoreT<ST>::CT;
-    Coef<T> C;
-    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
-    emit(0, eval_rest<L, COLL, T>(C, h[0]));
+    if constexpr (COLL == COLL_REG) {
+        emit(0, C.ce[0]);
+    } else {
+        emit(0, eval_rest<L, COLL, T>(C, h[0]));
+    }
     if constexpr (COLL == COLL_REG && sizeof(T) == 4 && L::NP % 2 == 0) {
         const F2 E1 = f2(C.e1, C.e1), E2 = f2(C.e2, C.e2), O0 = f2(C.o0, C.o0), O1 = f2(C.o1, C.o1);
 #pragma unroll
@@ -569,11 +631,24 @@ __device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v
 #pragma unroll
         for (int k = 0; k < L::NP; ++k) {
             T op, omn;
-            eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
+            if constexpr (COLL == COLL_REG)
+                eval_pair<L, COLL, T>(C, k, (T)0, (T)0, op, omn);
+            else
+                eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
             emit(1 + 2 * k, op);
             emit(2 + 2 * k, omn);
         }
     }
+}
+
+// prepare + evaluation of one node (see emit_outputs).
+template <class L, class ST, int COLL, int WALL = 0, class Emit>
+__device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
+                                             float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
+                                             Emit&& emit) {
+    Coef<typename StoreT<ST>::CT> C;
+    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
+    emit_outputs<L, ST, COLL>(C, h, emit);
 }
 
 // prepare + evaluation + store of one node.

@@ -49,7 +49,7 @@ ROUND16 = {L.LBM_STORE_BF16: 2.0 ** -8, L.LBM_STORE_F16: 2.0 ** -11}
 
 def run_both(Q, nx, ny, tau, omega, kind, steps, *, lx=0, ly=0, mask=None, drive=L.LBM_DRIVE_WALL, u0=1e-3,
              eq_order=2, collision=L.LBM_COLL_REGULARIZED, storage=L.LBM_STORE_F64, init_exp=None, seed=0,
-             tile=None, n0_chunks=1, wall=L.LBM_SCHEME_BOUNCEBACK, layout=L.LBM_LAYOUT_AB):
+             tile=None, n0_chunks=1, wall=L.LBM_SCHEME_BOUNCEBACK, layout=L.LBM_LAYOUT_AB, variant=None):
     """Run `steps` steps on the GPU and on the oracle; returns (g_gpu, g_or, F_gpu, F_or, labels, g0)."""
     geom = L.make_geometry(kind=kind, lx=lx, ly=ly, drive=drive, u0=u0, mask=mask, eq_order=eq_order,
                            collision=collision, storage=storage, wall_scheme=wall, layout=layout)
@@ -66,6 +66,9 @@ def run_both(Q, nx, ny, tau, omega, kind, steps, *, lx=0, ly=0, mask=None, drive
         assert (L.lbm_get_labels(h) == lab_or).all()
         if tile:
             L.lbm_set_tile(h, *tile)
+        if variant is not None:
+            L.lbm_set_variant(h, variant)
+            assert L.lbm_info(h)["variant"] == variant
         if g0 is not None:
             L.lbm_set_state(h, g0)
         chunk = steps // n0_chunks
@@ -259,6 +262,55 @@ def test_parity_staged_variants(variant):
                       f=g_to_oracle_state(Q, g0), nthreads=orc.max_threads())
     assert_state_close(Q, g, oracle_state_to_g(Q, f), lab, L.LBM_STORE_F32, steps, g0)
     assert_force_close(F, F_or, Q, lab, L.LBM_STORE_F32, steps)
+
+
+# The multi-row staged kernels in 16-bit storage (the batch runs 26) against the oracle on 393 x 90:
+# staged interior tiles, an odd width (a ragged last tile on the plain path) and a 23-wide beam, so
+# that interior tiles hold solid and boundary nodes.
+STAGED16 = [18, 26, 27]
+
+
+@pytest.mark.parametrize("st", [L.LBM_STORE_BF16, L.LBM_STORE_F16])
+@pytest.mark.parametrize("variant", STAGED16)
+def test_parity_16bit_staged_variants_one_step(st, variant):
+    """One step from a 16-bit-exact state, body-force frame (stream offset on): each output is the
+    exact step rounded once to 16 bits."""
+    Q, nx, ny = 37, 393, 90
+    g_gpu, g_or, F_gpu, F_or, lab, g0 = run_both(Q, nx, ny, 0.9, 0.05, L.LBM_GEOM_BEAM, 1, lx=23, ly=19,
+                                                 drive=L.LBM_DRIVE_BODYFORCE, u0=2e-3, eq_order=4, storage=st,
+                                                 init_exp=-7, seed=21, variant=variant)
+    assert_state_close(Q, g_gpu, g_or, lab, st, 1, g0, 2e-3 * stream_offset_magnitude(Q, 2e-3, 0.05, 1, 4))
+    assert_force_close(F_gpu, F_or, Q, lab, st, 1)
+
+
+@pytest.mark.parametrize("variant", STAGED16)
+def test_parity_16bit_staged_variants_chained(variant):
+    """Eleven chained FP16 steps (moving wall, lab frame; two launches, so consecutive grids chain),
+    then the twelfth against one oracle step from the state the GPU reached: each output is that
+    exact step rounded once to 16 bits."""
+    Q, nx, ny, lx, ly, u0 = 37, 393, 90, 23, 19, 2e-3
+    geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=lx, ly=ly, drive=L.LBM_DRIVE_WALL, u0=u0, eq_order=4,
+                           storage=L.LBM_STORE_F16)
+    _, wts, _ = L.lbm_lattice_velocities(Q)
+    lab = orc.geometry_beam(nx, ny, lx, ly)
+    h0 = I.random_scaled_state(Q, nx, ny, -9, seed=22)
+    h0[:, lab != 0] = 0.0
+    h = L.lbm_create(Q, nx, ny, 0.9, 0.05, geom)
+    try:
+        L.lbm_set_variant(h, variant)
+        L.lbm_set_state(h, h0 * wts[:, None, None] * u0)
+        L.lbm_step(h, 5)
+        L.lbm_step(h, 6)
+        g11 = L.lbm_get_state(h)
+        L.lbm_step(h, 1)
+        g12 = L.lbm_get_state(h)
+        F = L.lbm_force_history(h)
+    finally:
+        L.lbm_destroy(h)
+    f, F_or = orc.run(Q, lab, 0.9, 0.05, u0, 1, eq_order=4, collision=orc.COLL_REG, drive=orc.DRIVE_WALL,
+                      f=g_to_oracle_state(Q, g11), n0=11, nthreads=orc.max_threads())
+    assert_state_close(Q, g12, oracle_state_to_g(Q, f), lab, L.LBM_STORE_F16, 1, g11)
+    assert_force_close(F[11:12], F_or, Q, lab, L.LBM_STORE_F16, 1)
 
 
 def test_repeat_runs_are_bitwise_identical():
