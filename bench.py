@@ -48,10 +48,10 @@ STORE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current step kernels,
 # from one ncu capture each (profiles/*.md); a kernel change invalidates its entry.
-TRAFFIC = {("beam1024", 1): 156.397824e6 + 107.944704e6,        # step_kernel_occ<D2Q37, float, 1, 6>
-           ("beam1024x1", 1): 156.397824e6 + 107.944704e6,
-           ("beam1024x1", 2): 156.414208e6 + 106.665984e6,      # step_kernel_occ<D2Q37, float, 1, 7>
-           ("beam1024x1-f16", 26): 78.860288e6 + 35.606016e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
+TRAFFIC = {("beam1024", 1): 156.400384e6 + 108.256000e6,        # step_kernel_occ<D2Q37, float, 1, 6>
+           ("beam1024x1", 1): 156.400384e6 + 108.256000e6,
+           ("beam1024x1", 2): 156.415744e6 + 106.728448e6,      # step_kernel_occ<D2Q37, float, 1, 7>
+           ("beam1024x1-f16", 26): 78.831872e6 + 35.435776e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 

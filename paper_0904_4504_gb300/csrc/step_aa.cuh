@@ -82,14 +82,12 @@ __device__ __forceinline__ void aa_push(const InstDev& P, ST* A, int idx, const 
             S::st(A + i * plane + roff[R - cy_of<L>(i)] + col[R - cx_of<L>(i)], v);
         }
     };
-    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]));
-#pragma unroll
-    for (int k = 0; k < L::NP; ++k) {
-        T op, omn;
-        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        push(1 + 2 * k, op);
-        push(2 + 2 * k, omn);
-    }
+    emit_outputs<L, ST, COLL>(C, h, [&](int i, T v) {
+        if (i == 0)
+            S::st(A + idx, v);
+        else
+            push(i, v);
+    });
 }
 
 // Even step of one node: pull h_i = A[x - c_i][opp(i)], wall fix-up from the node's own plane i,
@@ -136,14 +134,8 @@ __device__ __forceinline__ void aa_local(const InstDev& P, ST* A, int x, int y, 
     Coef<T> C;
     double Fx = 0.0, Fy = 0.0;  // no fix-up on this step: stays zero
     prepare<L, ST, COLL, 0, OWN_NONE>(P, A, x, y, cls, P.dv, P.dv_f, h, Fx, Fy, C);
-    S::st(A + idx, eval_rest<L, COLL, T>(C, h[0]));
-#pragma unroll
-    for (int k = 0; k < L::NP; ++k) {
-        T op, omn;
-        eval_pair<L, COLL, T>(C, k, h[1 + 2 * k], h[2 + 2 * k], op, omn);
-        S::st(A + (2 + 2 * k) * plane + idx, op);
-        S::st(A + (1 + 2 * k) * plane + idx, omn);
-    }
+    // output i goes to plane opp(i)
+    emit_outputs<L, ST, COLL>(C, h, [&](int i, T v) { S::st(A + opp_of<L>(i) * plane + idx, v); });
 }
 
 // One launch = one step; PHASE 0 the even (pull-push) step, 1 the odd (local) one.  P.dst is the
