@@ -52,6 +52,10 @@ TRAFFIC = {("beam1024", 1): 156.400384e6 + 108.256000e6,        # step_kernel_oc
            ("beam1024x1", 1): 156.400384e6 + 108.256000e6,
            ("beam1024x1", 2): 156.415744e6 + 106.728448e6,      # step_kernel_occ<D2Q37, float, 1, 7>
            ("beam1024x1-f16", 26): 78.831872e6 + 35.435776e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
+# Thread instructions per fluid node (smsp__inst_executed.sum x 32 / fluid nodes) of the 16-bit step
+# kernel, from the same capture: with 16-bit storage the step is bound by instruction issue, so the
+# batched line also reports the issue rate against the SMs' issue peak.
+INST_PER_NODE = {("beam1024x1-f16", 26): 762.8}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 
@@ -178,6 +182,25 @@ def sweep_descs(L, storage, layout="ab"):
     return out
 
 
+def issue_roofline(bl):
+    """Warp instructions issued per second by the 16-bit step kernel of a batch line against the
+    SMs' issue peak (4 schedulers per SM, one warp instruction per scheduler per cycle, at the
+    median SM clock sampled during the run); None without a captured instruction count."""
+    import torch
+    ipn = INST_PER_NODE.get(("beam1024x1-f16", bl["config"].get("kernel_variant")))
+    mhz = (bl.get("clocks") or {}).get("sm_mhz")
+    if not ipn or not mhz:
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    achieved = bl["value"] * 1e6 * ipn / 32 / 1e9
+    peak = sms * 4 * mhz * 1e6 / 1e9
+    return {"bound": "alu", "inst_per_node": ipn, "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "peak_source": f"{sms} SMs x 4 schedulers x 1 warp instruction per cycle x {mhz:g} MHz (median SM clock "
+                           "of the run)",
+            "inst_source": "ncu smsp__inst_executed.sum of the kernel on one 1024^2 beam instance"}
+
+
 def run_batch(args, sub=False):
     import torch
     from paper_0904_4504_gb300 import lbm as L
@@ -194,10 +217,11 @@ def run_batch(args, sub=False):
     if args.batch_variant is not None:
         L.lbm_batch_set_variant(b, args.batch_variant)
     L.lbm_batch_set_stream(b, stream)
-    for _, d in descs:
-        L.lbm_batch_add(b, d)
+    slots = [L.lbm_batch_add(b, d) for _, d in descs]
     info0 = L.lbm_batch_info(b)
     fluid, bytes_step = info0["fluid_running"], info0["bytes_per_step"]
+    # the step kernel the instances run (streams mode: chosen per instance at admission)
+    used = sorted({L.lbm_info(L.lbm_batch_instance(b, k))["variant"] for k in slots})
 
     def run(n):
         left = n
@@ -264,7 +288,7 @@ def run_batch(args, sub=False):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
                        "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout,
-                       "kernel_variant": "default" if args.batch_variant is None else args.batch_variant},
+                       "kernel_variant": used[0] if len(used) == 1 else used},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
@@ -506,6 +530,7 @@ def run_ours(args):
                 "value": bl["value"], "unit": "MLUPS", "steps": bl["steps"], "ms_per_step": bl["ms_per_step"],
                 "roofline": bl["roofline"], "clocks": bl["clocks"], "gpu_launches": bl["gpu_launches"],
                 "speedup_vs_plain_fp32": round(bl["value"] / value, 4),
+                "issue": issue_roofline(bl),
                 "force_error_vs_oracle": "FP16 storage <= 1.6e-5 of the force amplitude (in-phase and quadrature, "
                                          "body and lab frame, tests/test_gpu_precision.py); target 1e-4"}
             extras["serving"] = {k: sl[k] for k in ("value", "unit", "config", "latency", "server", "clocks")}

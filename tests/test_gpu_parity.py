@@ -331,9 +331,16 @@ def test_repeat_runs_are_bitwise_identical():
 # GPU's own state at step n, compared at every node with the GPU's step n + 1
 # -------------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,storage,to", [(1024, L.LBM_STORE_F32, 0.01), (1024, L.LBM_STORE_F32, 10.0),
-                                          (2048, L.LBM_STORE_F16, 1.0), (2048, L.LBM_STORE_BF16, 0.1)])
-def test_full_size_one_step(n, storage, to):
+@pytest.mark.parametrize("n,storage,to,variant", [(1024, L.LBM_STORE_F32, 0.01, None),
+                                                  (1024, L.LBM_STORE_F32, 10.0, None),
+                                                  (1024, L.LBM_STORE_F32, 1.0, 2),
+                                                  (2048, L.LBM_STORE_F16, 1.0, None),
+                                                  (2048, L.LBM_STORE_BF16, 0.1, None),
+                                                  (1024, L.LBM_STORE_F16, 1.0, 26),
+                                                  (1024, L.LBM_STORE_BF16, 10.0, 26)])
+def test_full_size_one_step(n, storage, to, variant):
+    """variant: the kernel the batch's streams mode runs (2 for FP32, 26 for 16-bit storage) on the
+    largest instance of the 64-instance sweep; None: the default of lbm_create."""
     w = I.beam_d2q37_h4(to, n=n, storage=storage)
     tau, omega, _ = orc.params_from_tau_omega(37, to)
     geom = L.make_geometry(kind=w.geometry, lx=w.lx, ly=w.ly, drive=w.drive, u0=w.u0, eq_order=w.eq_order,
@@ -345,6 +352,8 @@ def test_full_size_one_step(n, storage, to):
     h0[:, lab != 0] = 0.0
     h = L.lbm_create(37, n, n, tau, omega, geom)
     try:
+        if variant is not None:
+            L.lbm_set_variant(h, variant)
         L.lbm_set_state(h, h0 * wts[:, None, None] * s)
         L.lbm_step(h, 7)                       # n0 = 7: the drive phase is not at zero
         g7 = L.lbm_get_state(h)
