@@ -51,11 +51,11 @@ STORE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 TRAFFIC = {("beam1024", 1): 156.400384e6 + 108.256000e6,        # step_kernel_occ<D2Q37, float, 1, 6>
            ("beam1024x1", 1): 156.400384e6 + 108.256000e6,
            ("beam1024x1", 2): 156.415744e6 + 106.728448e6,      # step_kernel_occ<D2Q37, float, 1, 7>
-           ("beam1024x1-f16", 26): 78.831872e6 + 35.435776e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
+           ("beam1024x1-f16", 27): 78.824192e6 + 35.493120e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 11>
 # Thread instructions per fluid node (smsp__inst_executed.sum x 32 / fluid nodes) of the 16-bit step
 # kernel, from the same capture: with 16-bit storage the step is bound by instruction issue, so the
 # batched line also reports the issue rate against the SMs' issue peak.
-INST_PER_NODE = {("beam1024x1-f16", 26): 762.8}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 12>
+INST_PER_NODE = {("beam1024x1-f16", 27): 758.4}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 11>
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 

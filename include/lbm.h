@@ -303,7 +303,7 @@ int lbm_batch_remove(lbm_batch* batch, int slot);
 int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
- * numbers; -1, the default: for D2Q37 the staged variant 26 with 16-bit storage and variant 2 with
+ * numbers; -1, the default: for D2Q37 the staged variant 27 with 16-bit storage and variant 2 with
  * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
  * support falls back to the plain kernel.  Ignored by the persistent mode.  LBM_EINVAL for a number
  * below -1. */

@@ -317,11 +317,11 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     // instance does not wait for a run of the batch that may be in flight
     if (b->mode == LBM_BATCH_PERSISTENT) sim_disable_stream_offset(sim);  // the kernel reads fixed params
     // default kernels, fastest measured in this mode: for D2Q37, the staged kernel with three rows
-    // per thread (26) for 16-bit storage and the plain kernel with 7 resident blocks per SM (2) for
+    // per thread (27) for 16-bit storage and the plain kernel with 7 resident blocks per SM (2) for
     // FP32; 16-bit D2Q9 takes the staged kernel 10; else the plain kernel
     const bool half = b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16;
     const int want = b->variant >= 0 ? b->variant
-                     : half ? (b->Q == 37 ? 26 : 10)
+                     : half ? (b->Q == 37 ? 27 : 10)
                      : (b->Q == 37 && b->storage == LBM_STORE_F32) ? 2 : 0;
     if (b->mode == LBM_BATCH_PERSISTENT || want == 0 || lbm_set_variant(sim, want) != LBM_OK)
         rc = lbm_set_tile(sim, b->bx, b->by);

@@ -36,7 +36,7 @@ def batch_kernel_variant(d, mode=L.LBM_BATCH_STREAMS):
     if mode != L.LBM_BATCH_STREAMS or g.layout != L.LBM_LAYOUT_AB or g.wall_scheme != L.LBM_SCHEME_BOUNCEBACK:
         return 0
     if g.storage in (L.LBM_STORE_BF16, L.LBM_STORE_F16):
-        return 26 if d.lattice == 37 else 10
+        return 27 if d.lattice == 37 else 10
     return 2 if (d.lattice == 37 and g.storage == L.LBM_STORE_F32) else 0
 
 
