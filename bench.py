@@ -316,7 +316,10 @@ def run_serve(args, sub=False):
     build()
     storage = STORE["f16"] if args.workload.endswith("-f16") else STORE["f32"]
     from paper_0904_4504_gb300.replicas import rank_slice
-    stream = rank_slice(I.serving_requests(), rank, args.requests)
+    reqs_all = I.serving_requests()
+    if args.serve_lattice:
+        reqs_all = [r for r in reqs_all if r.workload.lattice == args.serve_lattice]
+    stream = rank_slice(reqs_all, rank, args.requests)
     reqs, gpu_s = [], []
     peak, peak_kind = peaks()
     for r in stream:
@@ -335,7 +338,7 @@ def run_serve(args, sub=False):
         arrivals = np.cumsum(np.random.default_rng(I.SERVE_SEED + 1).exponential(1.0 / rate, len(reqs)))
     else:
         arrivals = np.array([a for a, _ in reqs]) - reqs[0][0]
-    srv = L.lbm_server_create(0, args.chunk)
+    srv = L.lbm_server_create(int(args.serve_budget_gb * 1e9), args.chunk)
     ids = []
     torch.cuda.synchronize()
     barrier(world)
@@ -357,8 +360,12 @@ def run_serve(args, sub=False):
     lat = np.array([r["done_s"] - r["submit_s"] for r in results])
     ok = all(r["status"] == 2 for r in results)
     lu = sum(r["steps"] * r["fluid_nodes"] for r in results)
+    # algorithmic bytes: one read and one write of every population of every fluid node per step
+    nbytes = sum(r["steps"] * r["fluid_nodes"] * 2 * q.workload.lattice * L.STORAGE_BYTES[storage]
+                 for r, q in zip(results, stream))
     span = max_over_ranks(makespan, world)
     value = lu * world / span / 1e6
+    achieved = nbytes * world / span / 1e9
     if rank == 0:
         line = {
             "metric": "aggregate MLUPS of the served requests (fluid lattice updates per second, submit of the first "
@@ -368,10 +375,17 @@ def run_serve(args, sub=False):
             "scaling": "weak", "vs_baseline": None, "dtype": {v: k for k, v in STORE.items()}[storage],
             "data": "synthetic",
             "config": {"workload": args.workload, "requests": len(reqs), "offered_load": args.load or "as generated",
+                       "lattices": args.serve_lattice or "D2Q9 and D2Q37",
+                       "budget_gb": args.serve_budget_gb or "server default",
                        "steps_per_round": args.chunk, "parallelism": f"replicas x{world}", "layout": args.layout},
             "latency": {"p50_s": round(float(np.percentile(lat, 50)), 4),
                         "p99_s": round(float(np.percentile(lat, 99)), 4), "mean_s": round(float(lat.mean()), 4),
                         "max_s": round(float(lat.max()), 4)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": "step kernels of the running requests; the makespan (first submit to last "
+                                   "completion) includes the ramp and the tail",
+                         "bytes": nbytes},
             "server": {"completed": stats["completed"], "all_ok": ok, "busy_frac": round(stats["busy_s"] / span, 4),
                        "peak_running": stats["peak_running"], "peak_used_gb": round(stats["peak_used_bytes"] / 1e9, 3),
                        "total_lattice_updates": lu, "makespan_s": round(span, 3)},
@@ -522,6 +536,11 @@ def run_ours(args):
         a = copy.copy(args)
         a.workload, a.requests, a.load = "serve", args.requests, args.load
         sl = run_serve(a, sub=True)
+        # the served mixed-precision form at saturation: the request stream as generated offers
+        # 10-25x the GPU's capacity, so the server always has work
+        a = copy.copy(args)
+        a.workload, a.requests, a.load = "serve-f16", args.requests, 0.0
+        sm = run_serve(a, sub=True)
         if rank == 0:
             extras["batched_mixed_precision"] = {
                 "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024), "
@@ -534,6 +553,8 @@ def run_ours(args):
                 "force_error_vs_oracle": "FP16 storage <= 1.6e-5 of the force amplitude (in-phase and quadrature, "
                                          "body and lab frame, tests/test_gpu_precision.py); target 1e-4"}
             extras["serving"] = {k: sl[k] for k in ("value", "unit", "config", "latency", "server", "clocks")}
+            extras["serving_mixed_precision_saturated"] = {
+                k: sm[k] for k in ("value", "unit", "config", "roofline", "latency", "server", "clocks")}
     if rank == 0:
         w0 = wl[0]
         line = {
@@ -650,6 +671,10 @@ def main():
                     help="population layout: two buffers (ab) or one buffer updated in place (aa)")
     ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64, serve)")
     ap.add_argument("--requests", type=int, default=24, help="requests per rank (serve)")
+    ap.add_argument("--serve-lattice", type=int, default=0, choices=[0, 9, 37],
+                    help="serve: only the requests of this lattice (0: all)")
+    ap.add_argument("--serve-budget-gb", type=float, default=0.0,
+                    help="serve: device memory the server may give to resident lattices (0: its default)")
     ap.add_argument("--load", type=float, default=0.7, help="offered load, fraction of capacity (serve; 0: as generated)")
     ap.add_argument("--sweep-steps", type=int, default=640, help="timed batch steps of the batched part of beam1024")
     ap.add_argument("--no-extras", action="store_true", help="beam1024: skip the batched and serving parts")

@@ -276,19 +276,29 @@ void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t
     cls.assign(N, NODE_BULK);
     body.assign(N, 0);
     wall.assign(N, 0);
-    // solid within R (periodic) of each node: separable dilation
-    std::vector<uint8_t> rownear(N, 0), near(N, 0);
-    for (int y = 0; y < ny; ++y)
+    // solid within R (periodic) of each node: separable dilation, scattered from the solid nodes
+    // along x, then the rows within R along y or-ed in; rows with no solid node are skipped (a large
+    // domain around a small body is mostly such rows).  nx, ny > R, so one +-n wraps.
+    std::vector<uint8_t> rowsolid(ny, 0), rownear(N, 0), near(N, 0);
+    for (int y = 0; y < ny; ++y) {
+        const uint8_t* L = lab.data() + (size_t)y * nx;
+        uint8_t* O = rownear.data() + (size_t)y * nx;
         for (int x = 0; x < nx; ++x) {
-            uint8_t v = 0;
-            for (int d = -H.R; d <= H.R && !v; ++d) v = lab[(size_t)y * nx + ((x + d) % nx + nx) % nx] != 0;
-            rownear[(size_t)y * nx + x] = v;
+            if (!L[x]) continue;
+            rowsolid[y] = 1;
+            for (int d = -H.R; d <= H.R; ++d) {
+                const int xs = x + d < 0 ? x + d + nx : (x + d >= nx ? x + d - nx : x + d);
+                O[xs] = 1;
+            }
         }
+    }
     for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            uint8_t v = 0;
-            for (int d = -H.R; d <= H.R && !v; ++d) v = rownear[(size_t)(((y + d) % ny + ny) % ny) * nx + x];
-            near[(size_t)y * nx + x] = v;
+        for (int d = -H.R; d <= H.R; ++d) {
+            const int ys = y + d < 0 ? y + d + ny : (y + d >= ny ? y + d - ny : y + d);
+            if (!rowsolid[ys]) continue;
+            const uint8_t* I = rownear.data() + (size_t)ys * nx;
+            uint8_t* O = near.data() + (size_t)y * nx;
+            for (int x = 0; x < nx; ++x) O[x] |= I[x];
         }
     n_fluid = n_boundary = 0;
     for (int y = 0; y < ny; ++y)
@@ -607,6 +617,16 @@ void sim_disable_stream_offset(lbm_sim* s) {
 void sim_advance(lbm_sim* s, long steps) {
     s->steps_done += steps;
     s->cur ^= (int)(steps & 1);
+}
+
+void sim_move_stream(lbm_sim* s, cudaStream_t stream) {
+    if (s->own_stream) {
+        // an owned stream is released only once its work is done (destroy does not wait for it)
+        cudaStreamSynchronize(s->stream);
+        cudaStreamDestroy(s->stream);
+    }
+    s->stream = stream;
+    s->own_stream = false;
 }
 
 }  // namespace lbm

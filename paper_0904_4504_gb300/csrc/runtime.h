@@ -53,5 +53,8 @@ int sim_reserve(lbm_sim* s, size_t steps);
 void sim_disable_stream_offset(lbm_sim* s);
 // Record that `steps` steps were run on the simulation's buffers by another launcher.
 void sim_advance(lbm_sim* s, long steps);
+// Issue the simulation's later work on `stream` (not owned) without waiting for its current stream:
+// the caller orders the two (the batch forks every sub-stream from one event per run).
+void sim_move_stream(lbm_sim* s, cudaStream_t stream);
 
 }  // namespace lbm
