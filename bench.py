@@ -537,9 +537,11 @@ def run_ours(args):
         a.workload, a.requests, a.load = "serve", args.requests, args.load
         sl = run_serve(a, sub=True)
         # the served mixed-precision form at saturation: the request stream as generated offers
-        # 10-25x the GPU's capacity, so the server always has work
+        # 10-25x the GPU's capacity, so the server always has work; a 6 GB device budget keeps a
+        # few dozen lattices resident, and 96 requests make the admit-as-others-finish steady state
+        # most of the run
         a = copy.copy(args)
-        a.workload, a.requests, a.load = "serve-f16", args.requests, 0.0
+        a.workload, a.requests, a.load, a.serve_budget_gb = "serve-f16", 96, 0.0, 6.0
         sm = run_serve(a, sub=True)
         if rank == 0:
             extras["batched_mixed_precision"] = {

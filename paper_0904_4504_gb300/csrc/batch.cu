@@ -24,7 +24,6 @@ namespace {
 
 struct Slot {
     lbm_sim* sim = nullptr;
-    int sub = 0;              // sub-stream the instance's steps are issued on (streams mode)
     long long start = 0;      // batch step of the instance's step 0
     long long nsteps = 0;
     double* d_drive = nullptr;   // [nsteps] drive, then [nsteps] of it in FP32 (same allocation)
@@ -349,7 +348,6 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     }
     Slot s;
     s.sim = sim;
-    s.sub = id % kSubStreams;
     s.start = b->gstep;
     s.nsteps = d->nsteps;
     s.d_drive = drv;
@@ -360,39 +358,6 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     b->dirty = true;
     *slot = id;
     return LBM_OK;
-}
-
-// Streams mode: spread the run's work over the sub-streams.  Each running instance's work in the
-// run (fluid nodes x its steps in the run), largest first, goes to the sub-stream with the least
-// work so far.  A run ends when its busiest sub-stream does, and instances of very different sizes
-// assigned by slot number leave most sub-streams idle well before that.  Moving an instance between
-// runs needs no wait: every sub-stream starts a run after the fork event, which follows all
-// sub-streams' work of the previous run.  Results do not depend on the assignment.
-static void balance_streams(lbm_batch* b, long steps) {
-    std::vector<std::pair<double, int>> work;
-    for (size_t k = 0; k < b->slots.size(); ++k) {
-        const Slot& s = b->slots[k];
-        if (!slot_live(s)) continue;
-        const long long lo = std::max<long long>(0, b->gstep - s.start);
-        const long long hi = std::min<long long>(s.nsteps, b->gstep + steps - s.start);
-        if (hi <= lo) continue;
-        work.emplace_back((double)sim_view(s.sim).n_fluid * (double)(hi - lo), (int)k);
-    }
-    std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
-        return a.first > c.first;
-    });
-    double load[kSubStreams] = {};
-    for (const auto& w : work) {
-        int j = 0;
-        for (int q = 1; q < kSubStreams; ++q)
-            if (load[q] < load[j]) j = q;
-        load[j] += w.first;
-        Slot& s = b->slots[w.second];
-        if (s.sub != j) {
-            sim_move_stream(s.sim, b->sub[j]);
-            s.sub = j;
-        }
-    }
 }
 
 int lbm_batch_run(lbm_batch* b, long steps) {
@@ -409,7 +374,6 @@ int lbm_batch_run(lbm_batch* b, long steps) {
         // batch stream's earlier work and the batch stream waits for theirs at the end
         BCUDA(cudaEventRecord(b->ev_fork, b->stream));
         for (int k = 0; k < kSubStreams; ++k) BCUDA(cudaStreamWaitEvent(b->sub[k], b->ev_fork, 0));
-        balance_streams(b, steps);
         for (long k = 0; k < steps; ++k) {
             for (Slot& s : b->slots) {
                 if (!slot_live(s)) continue;

@@ -269,51 +269,56 @@ static int gcd_int(int a, int b) {
 }
 
 // For every fluid node, the links whose pull source, or a lattice node strictly between source and
-// node, is solid; the first solid node met walking back from the node decides body or wall.
+// node, is solid; the first solid node met walking back from the node decides body or wall.  Only
+// rows within R of a row holding a solid node can have solid or boundary nodes; the others are bulk
+// fluid and are not visited (a large domain around a small body is mostly such rows).  `links`
+// lists the boundary nodes in increasing node order.
 void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t>& lab, std::vector<uint8_t>& cls,
-                 std::vector<uint64_t>& body, std::vector<uint64_t>& wall, size_t& n_fluid, size_t& n_boundary) {
+                 std::vector<LinkNode>& links, size_t& n_fluid) {
     const size_t N = (size_t)nx * ny;
     cls.assign(N, NODE_BULK);
-    body.assign(N, 0);
-    wall.assign(N, 0);
-    // solid within R (periodic) of each node: separable dilation, scattered from the solid nodes
-    // along x, then the rows within R along y or-ed in; rows with no solid node are skipped (a large
-    // domain around a small body is mostly such rows).  nx, ny > R, so one +-n wraps.
-    std::vector<uint8_t> rowsolid(ny, 0), rownear(N, 0), near(N, 0);
+    links.clear();
+    auto wrap = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };  // nx, ny > R
+    // solid within R along x of each node of the rows holding a solid, scattered from the solids
+    std::vector<uint8_t> rowsolid(ny, 0), rownear(N, 0), near(nx);
+    size_t n_solid = 0;
     for (int y = 0; y < ny; ++y) {
         const uint8_t* L = lab.data() + (size_t)y * nx;
         uint8_t* O = rownear.data() + (size_t)y * nx;
         for (int x = 0; x < nx; ++x) {
             if (!L[x]) continue;
             rowsolid[y] = 1;
-            for (int d = -H.R; d <= H.R; ++d) {
-                const int xs = x + d < 0 ? x + d + nx : (x + d >= nx ? x + d - nx : x + d);
-                O[xs] = 1;
-            }
+            ++n_solid;
+            for (int d = -H.R; d <= H.R; ++d) O[wrap(x + d, nx)] = 1;
         }
     }
-    for (int y = 0; y < ny; ++y)
+    n_fluid = N - n_solid;
+    for (int y = 0; y < ny; ++y) {
+        // solid within R of each node of row y: the rows within R along y or-ed together
+        bool any = false;
+        for (int d = -H.R; d <= H.R; ++d) any = any || rowsolid[wrap(y + d, ny)];
+        if (!any) continue;
+        std::fill(near.begin(), near.end(), 0);
         for (int d = -H.R; d <= H.R; ++d) {
-            const int ys = y + d < 0 ? y + d + ny : (y + d >= ny ? y + d - ny : y + d);
+            const int ys = wrap(y + d, ny);
             if (!rowsolid[ys]) continue;
             const uint8_t* I = rownear.data() + (size_t)ys * nx;
-            uint8_t* O = near.data() + (size_t)y * nx;
-            for (int x = 0; x < nx; ++x) O[x] |= I[x];
+            for (int x = 0; x < nx; ++x) near[x] |= I[x];
         }
-    n_fluid = n_boundary = 0;
-    for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const size_t node = (size_t)y * nx + x;
-            if (lab[node]) { cls[node] = NODE_SOLID; continue; }
-            ++n_fluid;
-            if (!near[node]) continue;
+            if (lab[node]) {
+                cls[node] = NODE_SOLID;
+                continue;
+            }
+            if (!near[x]) continue;
             uint64_t b = 0, w = 0;
             for (int i = 1; i < H.Q; ++i) {
                 const int cx = H.c[i][0], cy = H.c[i][1];
                 const int g = gcd_int(std::abs(cx), std::abs(cy));
                 for (int k = 1; k <= g; ++k) {
-                    const int sx = ((x - k * cx / g) % nx + nx) % nx;
-                    const int sy = ((y - k * cy / g) % ny + ny) % ny;
+                    const int sx = wrap(x - k * cx / g, nx);
+                    const int sy = wrap(y - k * cy / g, ny);
                     const uint8_t l = lab[(size_t)sy * nx + sx];
                     if (l) {
                         (l == LBM_BODY ? b : w) |= 1ull << i;
@@ -321,21 +326,20 @@ void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t
                     }
                 }
             }
-            body[node] = b;
-            wall[node] = w;
             if (b | w) {
                 cls[node] = NODE_BOUNDARY;
-                ++n_boundary;
+                links.push_back(LinkNode{node, b, w});
             }
         }
+    }
 }
 
 // Geometry-only part of the momentum exchange (the rest populations w_i rho0 bounced on body
 // links): -sum over body links of c_i 2 w_i rho0.
-void constant_force(const HostLattice& H, const std::vector<uint64_t>& body, double rho0, double& fx, double& fy) {
+void constant_force(const HostLattice& H, const std::vector<LinkNode>& links, double rho0, double& fx, double& fy) {
     fx = fy = 0.0;
-    for (size_t node = 0; node < body.size(); ++node) {
-        const uint64_t b = body[node];
+    for (const LinkNode& ln : links) {
+        const uint64_t b = ln.body;
         if (!b) continue;
         for (int i = 1; i < H.Q; ++i)
             if ((b >> i) & 1ull) {
@@ -345,20 +349,20 @@ void constant_force(const HostLattice& H, const std::vector<uint64_t>& body, dou
     }
 }
 
-void tile_slots(int nx, int ny, int bx, int by, const std::vector<uint64_t>& body, std::vector<int>& slot, int& ntx,
+void tile_slots(int nx, int ny, int bx, int by, const std::vector<LinkNode>& links, std::vector<int>& slot, int& ntx,
                 int& ntiles, int& nslots) {
     ntx = (nx + bx - 1) / bx;
     const int nty = (ny + by - 1) / by;
     ntiles = ntx * nty;
     slot.assign(ntiles, -1);
-    nslots = 0;
-    for (int t = 0; t < ntiles; ++t) {
-        const int tx = t % ntx, ty = t / ntx;
-        bool any = false;
-        for (int y = ty * by; y < std::min(ny, (ty + 1) * by) && !any; ++y)
-            for (int x = tx * bx; x < std::min(nx, (tx + 1) * bx) && !any; ++x) any = body[(size_t)y * nx + x] != 0;
-        if (any) slot[t] = nslots++;
+    for (const LinkNode& ln : links) {
+        if (!ln.body) continue;
+        const int x = (int)(ln.node % (size_t)nx), y = (int)(ln.node / (size_t)nx);
+        slot[(y / by) * ntx + x / bx] = 0;  // tile with body links
     }
+    nslots = 0;
+    for (int t = 0; t < ntiles; ++t)
+        if (slot[t] == 0) slot[t] = nslots++;
 }
 
 double drive_value(int drive, double u0, double omega, long n) {
@@ -414,7 +418,7 @@ struct lbm_sim {
     HostLattice lat{};
     size_t esize = 0;
     std::vector<uint8_t> labels;
-    std::vector<uint64_t> body_bits;
+    std::vector<LinkNode> link_nodes;  // boundary nodes and their link masks
     size_t n_fluid = 0, n_boundary = 0;
     double fconst[2] = {0, 0};
     // device memory
@@ -488,7 +492,7 @@ void free_sim(lbm_sim* s) {
 // (Re)build the per-tile force slots for the current tile shape.
 int setup_tiles(lbm_sim* s) {
     std::vector<int> slot;
-    tile_slots(s->nx, s->ny, s->bx, s->by, s->body_bits, slot, s->ntx, s->ntiles, s->nslots);
+    tile_slots(s->nx, s->ny, s->bx, s->by, s->link_nodes, slot, s->ntx, s->ntiles, s->nslots);
     cudaFree(s->d_tile_slot);
     cudaFree(s->d_partials);
     s->d_tile_slot = nullptr;
@@ -619,16 +623,6 @@ void sim_advance(lbm_sim* s, long steps) {
     s->cur ^= (int)(steps & 1);
 }
 
-void sim_move_stream(lbm_sim* s, cudaStream_t stream) {
-    if (s->own_stream) {
-        // an owned stream is released only once its work is done (destroy does not wait for it)
-        cudaStreamSynchronize(s->stream);
-        cudaStreamDestroy(s->stream);
-    }
-    s->stream = stream;
-    s->own_stream = false;
-}
-
 }  // namespace lbm
 
 extern "C" {
@@ -725,9 +719,9 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     g.mask = nullptr;
     s->geom = g;
     std::vector<uint8_t> cls;
-    std::vector<uint64_t> wall;
-    build_links(H, nx, ny, s->labels, cls, s->body_bits, wall, s->n_fluid, s->n_boundary);
-    constant_force(H, s->body_bits, g.rho0, s->fconst[0], s->fconst[1]);
+    build_links(H, nx, ny, s->labels, cls, s->link_nodes, s->n_fluid);
+    s->n_boundary = s->link_nodes.size();
+    constant_force(H, s->link_nodes, g.rho0, s->fconst[0], s->fconst[1]);
 
     const int align = (int)(128 / es);
     s->pitch = (nx + align - 1) / align * align;
@@ -759,27 +753,35 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
             return set_error(LBM_ECUDA, "memset");
         }
     }
-    // node classes and link masks in the padded layout
+    // node classes in the padded layout (padding solid); link masks zeroed on the device, then only
+    // the rows holding boundary nodes uploaded
     std::vector<uint8_t> cls_p(plane, NODE_SOLID);
-    std::vector<ulonglong2> links_p(plane, make_ulonglong2(0, 0));
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            const size_t k = (size_t)y * nx + x, kp = (size_t)y * s->pitch + x;
-            cls_p[kp] = cls[k];
-            links_p[kp] = make_ulonglong2(s->body_bits[k], wall[k]);
-        }
+    for (int y = 0; y < ny; ++y) std::copy_n(cls.data() + (size_t)y * nx, nx, cls_p.data() + (size_t)y * s->pitch);
     TRY_OR_FREE(dev_alloc(s, &s->d_cls, plane));
     TRY_OR_FREE(dev_alloc(s, &s->d_links, plane));
     TRY_OR_FREE(dev_alloc(s, &s->d_ticket, 1));
     TRY_OR_FREE(dev_alloc(s, &s->d_err, 1));
-    if (cudaMemcpy(s->d_cls, cls_p.data(), plane, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->d_links, links_p.data(), plane * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(s->d_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
+    bool up = cudaMemcpy(s->d_cls, cls_p.data(), plane, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(s->d_links, 0, plane * sizeof(ulonglong2)) == cudaSuccess &&
+              cudaMemset(s->d_ticket, 0, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(s->d_err, 0, sizeof(int)) == cudaSuccess;
+    s->h2d_bytes += plane;
+    std::vector<ulonglong2> row(s->pitch);
+    for (size_t k = 0; up && k < s->link_nodes.size();) {
+        const size_t y = s->link_nodes[k].node / (size_t)nx;
+        std::fill(row.begin(), row.end(), make_ulonglong2(0, 0));
+        for (; k < s->link_nodes.size() && s->link_nodes[k].node / (size_t)nx == y; ++k) {
+            const LinkNode& ln = s->link_nodes[k];
+            row[ln.node % (size_t)nx] = make_ulonglong2(ln.body, ln.wall);
+        }
+        up = cudaMemcpy(s->d_links + y * s->pitch, row.data(), s->pitch * sizeof(ulonglong2),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+        s->h2d_bytes += s->pitch * sizeof(ulonglong2);
+    }
+    if (!up) {
         free_sim(s);
         return set_error(LBM_ECUDA, "upload of geometry failed");
     }
-    s->h2d_bytes += plane * (1 + sizeof(ulonglong2));
 
     InstDev& d = s->dev;
     d.cls = s->d_cls;

@@ -25,10 +25,16 @@ int set_error(int code, const char* fmt, ...);
 void clear_error();
 const char* last_error();
 int build_labels(int Q, int nx, int ny, const lbm_geometry& g, std::vector<uint8_t>& lab);
+// A fluid node with blocked links: its offset in the unpadded grid (y nx + x) and link masks (bit i:
+// link i pulls from, or passes through, a solid node of the body, or of a static wall).
+struct LinkNode {
+    size_t node;
+    uint64_t body, wall;
+};
 void build_links(const HostLattice& H, int nx, int ny, const std::vector<uint8_t>& lab, std::vector<uint8_t>& cls,
-                 std::vector<uint64_t>& body, std::vector<uint64_t>& wall, size_t& n_fluid, size_t& n_boundary);
-void constant_force(const HostLattice& H, const std::vector<uint64_t>& body, double rho0, double& fx, double& fy);
-void tile_slots(int nx, int ny, int bx, int by, const std::vector<uint64_t>& body, std::vector<int>& slot, int& ntx,
+                 std::vector<LinkNode>& links, size_t& n_fluid);
+void constant_force(const HostLattice& H, const std::vector<LinkNode>& links, double rho0, double& fx, double& fy);
+void tile_slots(int nx, int ny, int bx, int by, const std::vector<LinkNode>& links, std::vector<int>& slot, int& ntx,
                 int& ntiles, int& nslots);
 double drive_value(int drive, double u0, double omega, long n);
 int fit_sincos(const double* fx, size_t stride, long n0, long n1, double omega, double coef[3]);
@@ -53,8 +59,5 @@ int sim_reserve(lbm_sim* s, size_t steps);
 void sim_disable_stream_offset(lbm_sim* s);
 // Record that `steps` steps were run on the simulation's buffers by another launcher.
 void sim_advance(lbm_sim* s, long steps);
-// Issue the simulation's later work on `stream` (not owned) without waiting for its current stream:
-// the caller orders the two (the batch forks every sub-stream from one event per run).
-void sim_move_stream(lbm_sim* s, cudaStream_t stream);
 
 }  // namespace lbm
