@@ -219,6 +219,19 @@ int lbm_autotune(lbm_sim* sim, int steps, lbm_tune_entry* best);
  * Any output may be NULL.  Returns Q, or LBM_EINVAL. */
 int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta);
 
+/* Node classes and blocked-link masks of a geometry on an nx x ny periodic grid, computed on the
+ * host (no GPU, no simulation): the wall rule of Eq. 12 as lbm_create applies it.  Link i of a
+ * fluid node is blocked when its pull source, or a lattice node strictly between source and node,
+ * is solid; the first solid node met walking back from the node makes it a body link (label
+ * LBM_BODY: bit i of body) or a static-wall link (bit i of wall).  cls: 0 bulk fluid, 1 solid, 2
+ * fluid with a blocked link.  Outputs are ny*nx row-major; any may be null; count: the elements
+ * each non-null output holds (at least nx*ny).  n_fluid, n_boundary (may be null): the counts
+ * lbm_info reports.  Reads the geometry's kind, lx, ly and mask only.  LBM_EINVAL for a bad
+ * lattice, grid, geometry kind or a short output. */
+int lbm_geometry_links(int lattice, int nx, int ny, const lbm_geometry* geom, unsigned char* cls,
+                       unsigned long long* body, unsigned long long* wall, size_t count, size_t* n_fluid,
+                       size_t* n_boundary);
+
 /*
  * Lattice parameters for a nondimensional frequency tau_omega = (tau - 1/2) omega (Sec. 6:
  * tau = mu/p = nu/theta): the period is P = max(p_min, ceil(2 pi delta_min / sqrt(2 theta

@@ -629,6 +629,36 @@ extern "C" {
 
 const char* lbm_last_error(void) { return last_error(); }
 
+int lbm_geometry_links(int lattice, int nx, int ny, const lbm_geometry* geom, unsigned char* cls,
+                       unsigned long long* body, unsigned long long* wall, size_t count, size_t* n_fluid,
+                       size_t* n_boundary) {
+    clear_error();
+    HostLattice H;
+    if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "unknown lattice %d", lattice);
+    if (!geom) return set_error(LBM_EINVAL, "null geometry");
+    if (nx < 2 * H.R + 1 || ny < 2 * H.R + 1)
+        return set_error(LBM_EINVAL, "grid %dx%d below %d nodes per side", nx, ny, 2 * H.R + 1);
+    if ((long long)nx * ny > (1ll << 31) / 2) return set_error(LBM_EINVAL, "grid %dx%d too large", nx, ny);
+    const size_t N = (size_t)nx * ny;
+    if ((cls || body || wall) && count < N) return set_error(LBM_EINVAL, "outputs hold %zu < %zu nodes", count, N);
+    std::vector<uint8_t> lab, c;
+    std::vector<LinkNode> links;
+    size_t nf = 0;
+    int rc = build_labels(lattice, nx, ny, *geom, lab);
+    if (rc) return rc;
+    build_links(H, nx, ny, lab, c, links, nf);
+    if (cls) std::copy(c.begin(), c.end(), cls);
+    if (body) std::fill(body, body + N, 0ull);
+    if (wall) std::fill(wall, wall + N, 0ull);
+    for (const LinkNode& ln : links) {
+        if (body) body[ln.node] = ln.body;
+        if (wall) wall[ln.node] = ln.wall;
+    }
+    if (n_fluid) *n_fluid = nf;
+    if (n_boundary) *n_boundary = links.size();
+    return LBM_OK;
+}
+
 int lbm_lattice_velocities(int lattice, int* c_xy, double* w, double* theta) {
     HostLattice H;
     if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "unknown lattice %d", lattice);

@@ -171,6 +171,10 @@ def lib():
             "lbm_get_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t]),
             "lbm_set_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t]),
             "lbm_get_labels": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ubyte), ctypes.c_size_t]),
+            "lbm_geometry_links": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lbm_geometry),
+                                                  ctypes.POINTER(ctypes.c_ubyte), ctypes.POINTER(ctypes.c_ulonglong),
+                                                  ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_size_t,
+                                                  ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
             "lbm_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_info_t)]),
             "lbm_set_tile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
             "lbm_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -328,6 +332,20 @@ def lbm_get_state(sim: int) -> np.ndarray:
 def lbm_set_state(sim: int, g: np.ndarray) -> None:
     g = np.ascontiguousarray(g, dtype=np.float64)
     _check(lib().lbm_set_state(sim, _dp(g), g.size))
+
+
+def lbm_geometry_links(lattice: int, nx: int, ny: int, geom) -> tuple:
+    """(cls, body, wall, n_fluid, n_boundary) of a geometry on the host: node classes (ny, nx) uint8
+    and blocked-link masks (ny, nx) uint64 (bit i: direction i of lbm_lattice_velocities)."""
+    cls = np.zeros((ny, nx), dtype=np.uint8)
+    body = np.zeros((ny, nx), dtype=np.uint64)
+    wall = np.zeros((ny, nx), dtype=np.uint64)
+    nf, nb = ctypes.c_size_t(), ctypes.c_size_t()
+    u64 = ctypes.POINTER(ctypes.c_ulonglong)
+    _check(lib().lbm_geometry_links(lattice, nx, ny, ctypes.byref(geom), cls.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                    body.ctypes.data_as(u64), wall.ctypes.data_as(u64), cls.size, ctypes.byref(nf),
+                                    ctypes.byref(nb)))
+    return cls, body, wall, nf.value, nb.value
 
 
 def lbm_get_labels(sim: int) -> np.ndarray:

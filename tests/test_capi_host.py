@@ -111,3 +111,78 @@ def test_create_rejects_bad_wall_scheme():
     with pytest.raises(L.LbmError) as e:
         L.lbm_create(37, 64, 64, 0.8, 0.1, geom)
     assert e.value.code == L.LBM_EINVAL and "wall scheme" in L.lbm_last_error()
+
+
+def _links_brute(Q, lab):
+    """Eq. 12's blocked links as lbm_create applies them (node-return bounce-back), written out per
+    node and direction: link i of fluid node x is blocked when x - c_i, or a lattice node strictly
+    between, is solid; the first solid met walking back from x decides body (label 1) or wall."""
+    c, _, _ = L.lbm_lattice_velocities(Q)
+    ny, nx = lab.shape
+    cls = np.zeros((ny, nx), dtype=np.uint8)
+    body = np.zeros((ny, nx), dtype=np.uint64)
+    wall = np.zeros((ny, nx), dtype=np.uint64)
+    for y in range(ny):
+        for x in range(nx):
+            if lab[y, x]:
+                cls[y, x] = 1
+                continue
+            b = w = 0
+            for i in range(1, Q):
+                cx, cy = int(c[i, 0]), int(c[i, 1])
+                g = math.gcd(abs(cx), abs(cy))
+                for k in range(1, g + 1):
+                    l = lab[(y - k * cy // g) % ny, (x - k * cx // g) % nx]
+                    if l:
+                        if l == L.LBM_BODY:
+                            b |= 1 << i
+                        else:
+                            w |= 1 << i
+                        break
+            body[y, x], wall[y, x] = b, w
+            if b or w:
+                cls[y, x] = 2
+    return cls, body, wall
+
+
+@pytest.mark.parametrize("case", ["beam37", "plate37", "mask37", "mask9", "small37", "wide37"])
+def test_geometry_links_match_the_wall_rule(case):
+    """The host geometry of lbm_create (classes and link masks, computed only near the solids)
+    against the rule written out node by node, on grids whose solids reach the periodic edges."""
+    rng = np.random.default_rng(7)
+    if case == "beam37":
+        Q, nx, ny, geom = 37, 45, 31, L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=9, ly=5)
+    elif case == "plate37":
+        Q, nx, ny, geom = 37, 12, 23, L.make_geometry(kind=L.LBM_GEOM_PLATE)
+    elif case in ("mask37", "mask9"):
+        Q, nx, ny = (37, 41, 29) if case == "mask37" else (9, 33, 19)
+        m = np.where(rng.random((ny, nx)) < 0.04, rng.integers(1, 3, (ny, nx)), 0).astype(np.uint8)
+        geom = L.make_geometry(kind=L.LBM_GEOM_MASK, mask=m)
+    elif case == "small37":
+        m = np.zeros((7, 7), dtype=np.uint8)
+        m[3, 3] = L.LBM_BODY
+        Q, nx, ny, geom = 37, 7, 7, L.make_geometry(kind=L.LBM_GEOM_MASK, mask=m)
+    else:
+        m = np.zeros((7, 60), dtype=np.uint8)
+        m[0, 10:14] = L.LBM_WALL
+        m[6, 50] = L.LBM_BODY
+        Q, nx, ny, geom = 37, 60, 7, L.make_geometry(kind=L.LBM_GEOM_MASK, mask=m)
+    cls, body, wall, nf, nb = L.lbm_geometry_links(Q, nx, ny, geom)
+    if case == "beam37":
+        lab = orc.geometry_beam(nx, ny, 9, 5)
+    elif case == "plate37":
+        lab = orc.geometry_plate(Q, nx, ny)
+    else:
+        lab = np.asarray(geom._mask_ref)
+    c_ref, b_ref, w_ref = _links_brute(Q, lab)
+    assert (cls == c_ref).all()
+    assert (body == b_ref).all() and (wall == w_ref).all()
+    assert nf == int((lab == 0).sum()) and nb == int((c_ref == 2).sum())
+
+
+def test_geometry_links_rejects_bad_input():
+    geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=4, ly=4)
+    with pytest.raises(L.LbmError):
+        L.lbm_geometry_links(37, 6, 20, geom)       # below 2R + 1 nodes per side
+    with pytest.raises(L.LbmError):
+        L.lbm_geometry_links(11, 20, 20, geom)      # no such lattice
