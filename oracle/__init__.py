@@ -76,6 +76,10 @@ def _load():
         lib.oracle_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, dp]
         lib.oracle_project.argtypes = [ctypes.c_int, dp, dp, dp]
+        lib.oracle_source.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp,
+                                       ctypes.c_double, dp]
         lib.oracle_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_long, ctypes.c_long, dp, dp, ctypes.c_int]
         lib.oracle_max_threads.argtypes = []
         _lib = lib
@@ -117,6 +121,25 @@ def project(Q: int, fadv: np.ndarray, feq: np.ndarray) -> np.ndarray:
     out = np.zeros(Q)
     if _load().oracle_project(Q, _dptr(fadv), _dptr(feq), _dptr(out)):
         raise ValueError("bad lattice")
+    return out
+
+
+def source(Q: int, tau: float, ux: float, uy: float, Fx: float, Fy: float) -> np.ndarray:
+    """Body-force source S_i of the time step (Guo-type, half-force velocity u; see lbm_oracle.c)."""
+    out = np.zeros(Q)
+    if _load().oracle_source(Q, tau, ux, uy, Fx, Fy, _dptr(out)):
+        raise ValueError("bad lattice or tau")
+    return out
+
+
+def collide(Q: int, eq_order: int, collision: int, tau: float, fadv: np.ndarray, gx: float = 0.0) -> np.ndarray:
+    """One node's collision from its advected populations, exactly as the time step does it: Eq. 16
+    (half-force velocity with the body force rho gx along x), Eq. 15, then Eq. 18 + 19 (collision 1)
+    or the BGK step (collision 0), plus the source."""
+    fadv = np.ascontiguousarray(fadv, dtype=np.float64)
+    out = np.zeros(Q)
+    if _load().oracle_collide(Q, eq_order, collision, tau, _dptr(fadv), gx, _dptr(out)):
+        raise ValueError("bad arguments")
     return out
 
 

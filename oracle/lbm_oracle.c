@@ -172,6 +172,67 @@ int oracle_project(int Q, const double* fadv, const double* feq, double* fne) {
     return 0;
 }
 
+/* Guo-type body-force source (the paper moves the wall instead; the body-frame drive is a reading
+ * of this build): with the fluid force density F = rho g and the half-force velocity u,
+ *   S_i = (1 - 1/(2 tau)) w_i [ c_i.F/theta + ((c_i.u)(c_i.F) - theta u.F)/theta^2 ],
+ * whose moments are 0, (1 - 1/(2 tau)) F and (1 - 1/(2 tau)) (uF + Fu). */
+static void guo_source(const olat* L, double tau, double ux, double uy, double Fbx, double Fby, double* S) {
+    int i;
+    double th = L->theta;
+    for (i = 0; i < L->Q; ++i) {
+        double cx = L->c[i][0], cy = L->c[i][1];
+        double cu = cx * ux + cy * uy, cF = cx * Fbx + cy * Fby, uF = ux * Fbx + uy * Fby;
+        S[i] = (1.0 - 0.5 / tau) * L->w[i] * (cF / th + (cu * cF - th * uF) / (th * th));
+    }
+}
+
+int oracle_source(int Q, double tau, double ux, double uy, double Fx, double Fy, double* S) {
+    olat L;
+    if (build_lattice(Q, &L) || !(tau > 0.5)) return -1;
+    guo_source(&L, tau, ux, uy, Fx, Fy, S);
+    return 0;
+}
+
+/* Collision of one node from its advected populations fadv (after the wall rule): Eq. 16 (with
+ * the half-force velocity u = (sum f c + F/2)/rho when a body force g acts, F = rho g along x),
+ * Eq. 15 (or its 4th-order continuation), then Eq. 18 with the projection of Eq. 19 (collision 1)
+ * or the explicit BGK step of Eq. 14 (collision 0), plus the source S_i when g != 0. */
+static void collide(const olat* L, int eq_order, int collision, double tau, const double* fadv, double gx,
+                    double* fout) {
+    int i, Q = L->Q;
+    double feq[OQMAX], fne[OQMAX], S[OQMAX];
+    double rho = 0, jx = 0, jy = 0, ux, uy, Fbx, Fby;
+    for (i = 0; i < Q; ++i) {
+        rho += fadv[i];
+        jx += fadv[i] * L->c[i][0];
+        jy += fadv[i] * L->c[i][1];
+    }
+    Fbx = rho * gx;
+    Fby = 0.0;
+    ux = (jx + 0.5 * Fbx) / rho;
+    uy = (jy + 0.5 * Fby) / rho;
+    equilibrium(L, eq_order, rho, ux, uy, feq);
+    if (collision == 1) project_nonequilibrium(L, fadv, feq, fne);
+    for (i = 0; i < Q; ++i) S[i] = 0.0;
+    if (gx != 0.0) guo_source(L, tau, ux, uy, Fbx, Fby, S);
+    for (i = 0; i < Q; ++i) {
+        if (collision == 1)
+            fout[i] = feq[i] + (1.0 - 1.0 / tau) * fne[i] + S[i];   /* Eq. 18 */
+        else
+            fout[i] = fadv[i] - (fadv[i] - feq[i]) / tau + S[i];    /* Eq. 14, explicit step */
+    }
+}
+
+/* One node's collision for the test suite (same code as the time step). */
+int oracle_collide(int Q, int eq_order, int collision, double tau, const double* fadv, double gx, double* fout) {
+    olat L;
+    if (build_lattice(Q, &L) || (eq_order != 2 && eq_order != 4) || (collision != 0 && collision != 1) ||
+        !(tau > 0.5))
+        return -1;
+    collide(&L, eq_order, collision, tau, fadv, gx, fout);
+    return 0;
+}
+
 typedef struct {
     int Q;                       /* 9 or 37                                                   */
     int nx, ny;                  /* periodic box; walls are solid labels inside it             */
@@ -197,9 +258,9 @@ static int gcd_int(int a, int b) {
 static void node_update(const olat* L, const oracle_params* p, const double* f, double* fout, int x, int y,
                         double uw, double gx, double* Fx, double* Fy) {
     int Q = L->Q, i, k;
-    double fadv[OQMAX], feq[OQMAX], fne[OQMAX];
+    double fadv[OQMAX];
     const double* fx = f + ((size_t)y * p->nx + x) * Q;
-    double th = L->theta, rho = 0, jx = 0, jy = 0, ux, uy, Fbx, Fby;
+    double th = L->theta;
 
     /* Eq. 17; links blocked by a solid get Eq. 12 or Eq. 11 below */
     int blocked[OQMAX];
@@ -243,31 +304,7 @@ static void node_update(const olat* L, const oracle_params* p, const double* f, 
             *Fx += -L->c[i][0] * (fx[L->opp[i]] + fadv[i]);
             *Fy += -L->c[i][1] * (fx[L->opp[i]] + fadv[i]);
         }
-    /* Eq. 16 */
-    for (i = 0; i < Q; ++i) {
-        rho += fadv[i];
-        jx += fadv[i] * L->c[i][0];
-        jy += fadv[i] * L->c[i][1];
-    }
-    Fbx = rho * gx;
-    Fby = 0.0;
-    ux = (jx + 0.5 * Fbx) / rho;
-    uy = (jy + 0.5 * Fby) / rho;
-    equilibrium(L, p->eq_order, rho, ux, uy, feq);
-    if (p->collision == 1) project_nonequilibrium(L, fadv, feq, fne);
-    for (i = 0; i < Q; ++i) {
-        double cx = L->c[i][0], cy = L->c[i][1], src = 0.0, cu, cF, uF;
-        if (gx != 0.0) {
-            cu = cx * ux + cy * uy;
-            cF = cx * Fbx + cy * Fby;
-            uF = ux * Fbx + uy * Fby;
-            src = (1.0 - 0.5 / p->tau) * L->w[i] * (cF / th + (cu * cF - th * uF) / (th * th));
-        }
-        if (p->collision == 1)
-            fout[i] = feq[i] + (1.0 - 1.0 / p->tau) * fne[i] + src;   /* Eq. 18 */
-        else
-            fout[i] = fadv[i] - (fadv[i] - feq[i]) / p->tau + src;    /* Eq. 14, explicit step */
-    }
+    collide(L, p->eq_order, p->collision, p->tau, fadv, gx, fout);
 }
 
 /* Advance the post-collision state f (ny*nx*Q, full populations, AoS) from step n0 by nsteps

@@ -109,6 +109,74 @@ def test_projection_is_the_hermite_projection(Q):
 
 
 # ------------------------------------------------------------------------------------------------
+# body-force source (Guo-type, half-force velocity): its moments, and the moments of one node's
+# collision with the force on.  The closed forms follow from the lattice's Gaussian moments,
+# sum w c_a c_b = theta d_ab and sum w c_a c_b c_c c_d = theta^2 (d_ab d_cd + d_ac d_bd + d_ad d_bc)
+# (exact for both lattices): for S_i = k w_i [c.F/theta + ((c.u)(c.F) - theta u.F)/theta^2],
+#   sum S = 0,   sum S c = k F,   sum S c c = k (u F + F u),   k = 1 - 1/(2 tau).
+# A flipped sign or a wrong factor on either term of S fails one of these.
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q", [37, 9])
+def test_force_source_moments(Q):
+    c, w, th = orc.lattice(Q)
+    rng = np.random.default_rng(23)
+    for _ in range(25):
+        tau = rng.uniform(0.55, 5.0)
+        ux, uy, Fx, Fy = rng.uniform(-0.05, 0.05, 4)
+        S = orc.source(Q, tau, ux, uy, Fx, Fy)
+        k = 1.0 - 0.5 / tau
+        u, F = np.array([ux, uy]), np.array([Fx, Fy])
+        scale = np.abs(F).max()
+        assert abs(S.sum()) < 1e-15 * scale
+        first = np.array([np.sum(S * c[:, a]) for a in (0, 1)])
+        assert np.abs(first - k * F).max() < 1e-14 * scale
+        second = np.array([[np.sum(S * c[:, a] * c[:, b]) for b in (0, 1)] for a in (0, 1)])
+        exact = k * (np.outer(u, F) + np.outer(F, u))
+        assert np.abs(second - exact).max() < 1e-14 * scale, (second, exact)
+
+
+@pytest.mark.parametrize("Q,order,coll", [(37, 2, orc.COLL_REG), (37, 4, orc.COLL_REG), (37, 4, orc.COLL_BGK),
+                                          (9, 2, orc.COLL_REG), (9, 2, orc.COLL_BGK)])
+def test_collision_with_body_force_moments(Q, order, coll):
+    """One node's collision at random (rho, j, Pi) and force F = rho g x: with the half-force velocity
+    u = (j + F/2)/rho,
+      mass:      sum f* = rho;
+      momentum:  sum f* c = j + F  (the source adds (1 - 1/2tau) F, the retained first moment
+                 (1 - 1/tau) J^ne with J^ne = -F/2 the rest: exact growth by F per step);
+      stress (regularized): sum f* c c = rho theta I + rho u u + (1 - 1/tau)(Pi - rho theta I - rho u u)
+                 + (1 - 1/(2 tau))(u F + F u).
+    The projection's first Hermite moment is also checked directly: sum fne c = J^ne = -F/2."""
+    c, w, th = orc.lattice(Q)
+    rng = np.random.default_rng(29)
+    for _ in range(20):
+        tau = rng.uniform(0.55, 4.0)
+        rho = rng.uniform(0.95, 1.05)
+        feq0 = orc.equilibrium(Q, 2, rho, *rng.uniform(-0.03, 0.03, 2))
+        fadv = feq0 + 2e-3 * w * rng.standard_normal(Q)
+        gx = rng.uniform(-1e-3, 1e-3)
+        rho = fadv.sum()
+        j = np.array([np.sum(fadv * c[:, 0]), np.sum(fadv * c[:, 1])])
+        F = np.array([rho * gx, 0.0])
+        u = (j + 0.5 * F) / rho
+        fout = orc.collide(Q, order, coll, tau, fadv, gx)
+        assert abs(fout.sum() - rho) < 1e-14 * rho
+        jout = np.array([np.sum(fout * c[:, 0]), np.sum(fout * c[:, 1])])
+        assert np.abs(jout - (j + F)).max() < 1e-15 * rho, (jout, j + F)
+        # the projection keeps J^ne = sum (f^adv - f^eq) c = j - rho u = -F/2
+        feq = orc.equilibrium(Q, order, rho, *u)
+        fne = orc.project(Q, fadv, feq)
+        Jne = np.array([np.sum(fne * c[:, 0]), np.sum(fne * c[:, 1])])
+        assert np.abs(Jne + 0.5 * F).max() < 1e-15 * rho
+        if coll == orc.COLL_REG:
+            Pi = np.array([[np.sum(fadv * c[:, a] * c[:, b]) for b in (0, 1)] for a in (0, 1)])
+            Peq = rho * th * np.eye(2) + rho * np.outer(u, u)
+            exact = Peq + (1 - 1 / tau) * (Pi - Peq) + (1 - 0.5 / tau) * (np.outer(u, F) + np.outer(F, u))
+            Pout = np.array([[np.sum(fout * c[:, a] * c[:, b]) for b in (0, 1)] for a in (0, 1)])
+            assert np.abs(Pout - exact).max() < 1e-14 * rho, (Pout, exact)
+
+
+# ------------------------------------------------------------------------------------------------
 # conservation laws of the whole step
 # ------------------------------------------------------------------------------------------------
 
