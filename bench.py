@@ -216,6 +216,8 @@ def run_batch(args, sub=False):
     L.lbm_batch_set_mode(b, args.batch_mode)
     if args.batch_variant is not None:
         L.lbm_batch_set_variant(b, args.batch_variant)
+    if args.batch_segment:
+        L.lbm_batch_set_segment(b, args.batch_segment)
     L.lbm_batch_set_stream(b, stream)
     slots = [L.lbm_batch_add(b, d) for _, d in descs]
     info0 = L.lbm_batch_info(b)
@@ -263,6 +265,8 @@ def run_batch(args, sub=False):
         L.lbm_batch_set_mode(b, args.batch_mode)
         if args.batch_variant is not None:
             L.lbm_batch_set_variant(b, args.batch_variant)
+        if args.batch_segment:
+            L.lbm_batch_set_segment(b, args.batch_segment)
         slots = [L.lbm_batch_add(b, d) for _, d in descs]
         run(args.steps)
         L.lbm_batch_synchronize(b)
@@ -683,6 +687,8 @@ def main():
     ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
     ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
     ap.add_argument("--batch-variant", type=int, default=None, help="sweep64: step kernel of the streams mode")
+    ap.add_argument("--batch-segment", type=int, default=0,
+                    help="sweep64, persistent mode: tiles per work item (0: the library's default)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

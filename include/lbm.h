@@ -169,6 +169,10 @@ typedef struct {
     size_t h2d_bytes, d2h_bytes; /* host<->device bytes copied by the library so far               */
     int variant;                 /* step kernel in use, see lbm_set_variant                        */
     int layout;                  /* LBM_LAYOUT_AB or LBM_LAYOUT_AA                                 */
+    int force_1e4;               /* 1 if this storage type meets a force error of 1e-4 of the force
+                                    amplitude (in-phase and quadrature, against FP64) in the library's
+                                    precision study: FP64, FP32 and FP16; 0 for BF16, whose 8-bit
+                                    significand gives about 1.5e-3 on the 256^2 beam               */
 } lbm_info_t;
 
 int lbm_info(lbm_sim* sim, lbm_info_t* out);
@@ -244,12 +248,15 @@ int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, i
 /* ----------------------------------------------------------------------------------------------
  * Batches: many simulations of uneven sizes (a tau*omega and aspect-ratio sweep, or the requests
  * of a server) advanced together.  All instances of a batch share the lattice, storage type and
- * collision; each has its own grid, geometry, tau, omega, drive and length in steps.  In the
- * persistent mode a run of K steps is one cooperative launch (a node of a CUDA graph built once per
- * launch shape): its grid fills the GPU, walks the tiles of every unfinished instance and meets at
- * a grid barrier between steps.  Each barrier wait is bounded (about 2 s by default); a wait that
- * runs out sets an error flag, the kernel returns, and lbm_batch_synchronize reports LBM_ETIMEOUT.
- * In both modes every instance's arithmetic is that of lbm_step on the same instance.
+ * collision; each has its own grid, geometry, tau, omega, drive and length in steps (the tau*omega
+ * and aspect-ratio sweep of Sec. 6).  In the persistent mode a run of K steps is one launch of a
+ * persistent kernel, replayed through a CUDA graph (built once per grid size): its blocks take
+ * (step, tile) items of every running instance from a queue in step order, and a tile waits only
+ * for the tiles of its own instance within the lattice reach of it to have finished the previous
+ * step -- there is no grid-wide barrier, and steps of different instances (and of distant tiles of
+ * one instance) overlap.  Each wait is bounded (about 2 s by default); a wait that runs out sets
+ * an error flag, the kernel returns, and lbm_batch_synchronize reports LBM_ETIMEOUT.  In both modes
+ * every instance's arithmetic is that of lbm_step on the same instance with the same tile shape.
  * ---------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
 
@@ -257,8 +264,10 @@ typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
  *   LBM_BATCH_STREAMS     every instance step is a launch of the single-instance kernel (the
  *                         fastest variant for the storage type) on one of several parallel
  *                         streams, so that instances of different sizes overlap (the default);
- *   LBM_BATCH_PERSISTENT  one cooperative launch per run walks all instances' tiles for K steps
- *                         with a bounded grid barrier between steps, replayed through a CUDA graph. */
+ *   LBM_BATCH_PERSISTENT  one launch per run of the persistent kernel over all instances' tiles
+ *                         for K steps (per-tile step counters, no grid barrier), replayed through
+ *                         a CUDA graph: staged 64 x 3 tiles (the shape of variant 27) with 16-bit
+ *                         storage, plain 32 x 4 tiles otherwise (lbm_batch_set_variant). */
 enum { LBM_BATCH_STREAMS = 0, LBM_BATCH_PERSISTENT = 1 };
 
 /* One instance: the arguments of lbm_create plus the number of steps to run. */
@@ -277,7 +286,7 @@ typedef struct {
     long long batch_steps, launches;
     double lattice_updates;        /* fluid-node updates enqueued so far                        */
     size_t budget_bytes, used_bytes;
-    int max_blocks;                /* co-resident blocks of the cooperative grid                */
+    int max_blocks;                /* resident blocks of the persistent kernel on the whole GPU */
     int uses_graph;                /* 1 if runs are replayed through a CUDA graph               */
     int block_x, block_y;
     int mode;                      /* LBM_BATCH_STREAMS or LBM_BATCH_PERSISTENT                 */
@@ -298,8 +307,8 @@ int lbm_batch_add(lbm_batch* batch, const lbm_instance_desc* desc, int* slot);
  * `steps`; an instance stops after its own nsteps. */
 int lbm_batch_run(lbm_batch* batch, long steps);
 
-/* Wait for the enqueued runs.  LBM_ETIMEOUT if a barrier wait gave up (the states are then
- * undefined). */
+/* Wait for the enqueued runs.  LBM_ETIMEOUT if a wait of the persistent kernel gave up (the
+ * states are then undefined). */
 int lbm_batch_synchronize(lbm_batch* batch);
 
 /* Steps enqueued for an instance and its length. */
@@ -312,17 +321,27 @@ lbm_sim* lbm_batch_instance(lbm_batch* batch, int slot);
 /* Free an instance's memory (waits for the batch's stream). */
 int lbm_batch_remove(lbm_batch* batch, int slot);
 
-/* Choose the mode (before the first lbm_batch_add). */
+/* Choose the mode (before the first lbm_batch_add); the persistent mode picks its kernel here. */
 int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
  * numbers; -1, the default: for D2Q37 the staged variant 27 with 16-bit storage and variant 2 with
- * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An instance whose layout or wall scheme the variant does not
- * support falls back to the plain kernel.  Ignored by the persistent mode.  LBM_EINVAL for a number
- * below -1. */
+ * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An
+ * instance whose layout or wall scheme the variant does not support falls back to the plain
+ * kernel.  In the persistent mode (before the first lbm_batch_add) it picks the persistent
+ * kernel's tiles: 27 staged 64 x 3, 0 or 2 plain 32 x 4, -1 the default of the storage type;
+ * other numbers are LBM_EINVAL there.  LBM_EINVAL for a number below -1. */
 int lbm_batch_set_variant(lbm_batch* batch, int variant);
 
-/* Clock cycles a block waits at a grid barrier before giving up (test hook: 0 gives up at once). */
+/* Tiles per work item of the persistent kernel (default 4): its items are segments of this many
+ * consecutive tiles of one tile row, taken in row order, so that neighbouring tiles run at about the
+ * same time and share their halo reads in L2; longer segments spread the per-item cost (a queue
+ * atomic, the dependency check) over more tiles.  Fixed once the batch has run in the persistent
+ * mode (the row counters count segments).  LBM_EINVAL outside 1..1024 or after that. */
+int lbm_batch_set_segment(lbm_batch* batch, int tiles);
+
+/* Clock cycles a block of the persistent kernel waits for another tile's progress before giving
+ * up (test hook: 0 gives up at once). */
 int lbm_batch_set_barrier_limit(lbm_batch* batch, long long cycles);
 
 int lbm_batch_info(lbm_batch* batch, lbm_batch_info_t* out);
@@ -426,7 +445,11 @@ void lbm_server_destroy(lbm_server* server);
  * or two host threads) race and give wrong forces; serialize them.  The counter is cleared at
  * the start of every call, so a call that never completed does not affect the next one.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current; make that first call before any stream capture (a lookup that fails is
+ * not remembered: the next call tries again).
+ * A diverged run is not reported by this call's return code (lbm_step's LBM_ENONFINITE comes from
+ * a flag that lbm_synchronize reads; this call keeps no such state between calls): the force it
+ * writes is then non-finite, so callers check force_out for NaN or Inf.
  * Errors: LBM_EINVAL (null or aliased buffers, n < 0), LBM_ERANGE, LBM_ECUDA.
  */
 #define LBM_NOALLOC_MAX_SLOTS 8192

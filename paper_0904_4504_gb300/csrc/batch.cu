@@ -1,11 +1,14 @@
-// batch.cu -- many lattice instances of uneven sizes advanced by one persistent cooperative kernel
-// (lbm_batch_* in include/lbm.h).
+// batch.cu -- many lattice instances of uneven sizes advanced together (lbm_batch_* in include/lbm.h).
 //
 // Each instance is an ordinary simulation (lbm_create: geometry, buffers, force scratch and
-// history) plus a device drive table of its own length.  A run of K steps is one cooperative
-// launch of batch_kernel: its grid (every SM full) walks the tiles of all unfinished instances,
-// round robin, and meets at a bounded grid barrier between steps.  The launch is a node of a CUDA
-// graph that is built once per launch shape and replayed with new arguments.
+// history).  Two modes run them:
+//  * persistent: a run of K steps is one launch of the persistent kernel (pbatch.cuh), whose blocks
+//    take (step, tile) items of every running instance from a queue and wait only for the tiles
+//    within reach of theirs; each instance adds a table of its per-step constants, per-tile step
+//    counters and a ring of force slots.  The launch (queue reset + kernel) is a CUDA graph built
+//    once per grid size and replayed with new arguments.
+//  * streams: every instance's step is a launch of the single-instance kernel on one of 16
+//    parallel streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,11 +29,15 @@ struct Slot {
     lbm_sim* sim = nullptr;
     long long start = 0;      // batch step of the instance's step 0
     long long nsteps = 0;
-    double* d_drive = nullptr;   // [nsteps] drive, then [nsteps] of it in FP32 (same allocation)
+    // persistent mode: one allocation holding the per-step constants [nsteps], the tile-row
+    // segment counters [nty], the force ring [kRing][nslots], its tickets [kRing] and finish marks
+    // [kRing]
+    unsigned char* d_pb = nullptr;
+    size_t off_done = 0, off_ring = 0, off_tickets = 0, off_fin = 0;
     size_t bytes = 0;
 };
 
-constexpr long long kDefaultBarrierLimit = 4000000000ll;  // clock cycles (about 2 s at 2 GHz)
+constexpr long long kDefaultWaitLimit = 4000000000ll;  // clock cycles (about 2 s at 2 GHz)
 
 }  // namespace
 
@@ -49,30 +56,27 @@ struct lbm_batch {
     std::vector<Slot> slots;
     long long gstep = 0;
     // device arrays of the launch
-    BatchInst* d_insts = nullptr;
+    PInst* d_insts = nullptr;
     size_t insts_cap = 0;
-    int2* d_tiles = nullptr;
-    size_t tiles_cap = 0;
-    int ntiles = 0;
-    unsigned int* d_bar = nullptr;  // [0] count, [1] generation
+    int4* d_segs = nullptr;         // (instance, tile row, first tile, end tile) of the running instances
+    size_t segs_cap = 0;
+    int nsegs = 0;
+    int seg_tiles = 4;              // tiles per work item of the persistent kernel
+    int pinned_seg = 0;             // segment length fixed by the seg_tiles in use at the first run
+    unsigned long long* d_queue = nullptr;  // work-item counter of the persistent kernel
     int* d_err = nullptr;
-    long long bar_limit = kDefaultBarrierLimit;
+    long long wait_limit = kDefaultWaitLimit;
     bool dirty = true;
-    BatchKernelFn kernel = nullptr;
+    int path = -1;                  // persistent kernel: PB_STAGED or PB_PLAIN (-1: not chosen yet)
+    PbKernel kernel{};
     int max_blocks = 0;             // co-resident blocks of the whole GPU
-    // graph of one cooperative launch, re-parameterized for every run
+    // graph of one launch (queue reset, kernel), re-parameterized for every run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t node = nullptr;
     int graph_grid = 0;
     bool use_graph = true;
-    // launch arguments (addresses stay valid for the graph's lifetime)
-    const BatchInst* a_insts = nullptr;
-    const int2* a_tiles = nullptr;
-    int a_ntiles = 0;
-    long long a_step0 = 0;
-    int a_nsteps = 0;
-    GridBarrier a_bar{};
+    PbArgs a_args{};                // launch arguments (the address stays valid for the graph's lifetime)
     long long launches = 0;
     double lattice_updates = 0.0;   // fluid-node updates enqueued
 };
@@ -108,93 +112,126 @@ void free_graph(lbm_batch* b) {
     b->graph_grid = 0;
 }
 
-// Device bytes of one instance (populations, geometry arrays, force history, drive table).
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Layout of a persistent-mode instance's allocation (see Slot); returns its size.
+size_t pb_layout(long long nsteps, int nty, int nslots, Slot* s) {
+    size_t off = align_up((size_t)nsteps * sizeof(StepConst), 256);
+    const size_t done = off;
+    off = align_up(off + (size_t)nty * sizeof(int), 256);
+    const size_t ring = off;
+    off = align_up(off + (size_t)kRing * (size_t)std::max(1, nslots) * sizeof(double2), 256);
+    const size_t tickets = off;
+    off = align_up(off + kRing * sizeof(unsigned int), 256);
+    const size_t fin = off;
+    off = align_up(off + kRing * sizeof(int), 256);
+    if (s) {
+        s->off_done = done;
+        s->off_ring = ring;
+        s->off_tickets = tickets;
+        s->off_fin = fin;
+    }
+    return off;
+}
+
+// Device bytes of one instance (populations, geometry arrays, force history, and in the persistent
+// mode its step table, tile counters and force ring; the tile shape bx x by).
 size_t footprint(const HostLattice& H, int nx, int ny, int storage, int layout, long nsteps, int bx, int by) {
     const size_t es = storage_size(storage);
     const size_t align = 128 / es;
     const size_t pitch = (nx + align - 1) / align * align;
     const size_t plane = (size_t)ny * pitch;
     const size_t tiles = (size_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by);
-    const size_t hist = std::max<size_t>(1024, (size_t)nsteps);
+    const size_t hist = std::max<size_t>(1024, (size_t)nsteps + 1);
     const size_t nbuf = layout == LBM_LAYOUT_AA ? 1 : 2;
     return nbuf * plane * H.Q * es + plane * (1 + sizeof(ulonglong2)) + tiles * (sizeof(int) + 2 * sizeof(double2)) +
-           hist * sizeof(double2) + (size_t)nsteps * (sizeof(double) + sizeof(float)) + 4096;
+           hist * sizeof(double2) + pb_layout(nsteps, (int)tiles, (int)tiles, nullptr) + 4096;
 }
 
-// Rebuild the per-instance launch table and the tile list of the unfinished instances.
+// Rebuild the per-instance launch table and the row-segment list of the unfinished instances.
 int rebuild(lbm_batch* b) {
-    std::vector<BatchInst> insts(std::max<size_t>(1, b->slots.size()));
-    std::vector<int2> tiles;
+    std::vector<PInst> insts(std::max<size_t>(1, b->slots.size()));
+    std::vector<int4> segs;
     for (size_t k = 0; k < b->slots.size(); ++k) {
         const Slot& s = b->slots[k];
-        BatchInst& I = insts[k];
+        PInst& I = insts[k];
         std::memset((void*)&I, 0, sizeof(I));
-        I.nsteps = 0;
         if (!slot_live(s)) continue;
         const SimView v = sim_view(s.sim);
+        if (v.maps) std::memcpy((void*)I.maps, (const void*)v.maps, sizeof(I.maps));
         I.base = v.inst;
         I.buf[0] = v.buf[0];
         I.buf[1] = v.buf[1];
-        I.drive = s.d_drive;
-        I.drive_f = reinterpret_cast<const float*>(s.d_drive + s.nsteps);
+        I.steps = reinterpret_cast<const StepConst*>(s.d_pb);
         I.history = v.history;
+        I.done = reinterpret_cast<int*>(s.d_pb + s.off_done);
+        I.ring = reinterpret_cast<double2*>(s.d_pb + s.off_ring);
+        I.tickets = reinterpret_cast<unsigned int*>(s.d_pb + s.off_tickets);
+        I.fin = reinterpret_cast<int*>(s.d_pb + s.off_fin);
         I.start = s.start;
         I.nsteps = s.nsteps;
+        I.bx = v.bx;
+        I.by = v.by;
+        I.nty = (v.ny + v.by - 1) / v.by;
+        const int ntx = v.inst.ntx, S = b->seg_tiles;
+        I.nseg = (ntx + S - 1) / S;
         if (!slot_running(b, s)) continue;
-        for (int t = 0; t < v.inst.ntiles; ++t) tiles.push_back(make_int2((int)k, t));
+        for (int r = 0; r < I.nty; ++r)
+            for (int t0 = 0; t0 < ntx; t0 += S) segs.push_back(make_int4((int)k, r, t0, std::min(t0 + S, ntx)));
     }
     if (insts.size() > b->insts_cap) {
         cudaFree(b->d_insts);
         b->d_insts = nullptr;
-        BCUDA(cudaMalloc((void**)&b->d_insts, insts.size() * sizeof(BatchInst)));
+        BCUDA(cudaMalloc((void**)&b->d_insts, insts.size() * sizeof(PInst)));
         b->insts_cap = insts.size();
     }
-    if (tiles.size() > b->tiles_cap || !b->d_tiles) {
-        cudaFree(b->d_tiles);
-        b->d_tiles = nullptr;
-        const size_t cap = std::max<size_t>(tiles.size(), 1);
-        BCUDA(cudaMalloc((void**)&b->d_tiles, cap * sizeof(int2)));
-        b->tiles_cap = cap;
+    if (segs.size() > b->segs_cap || !b->d_segs) {
+        cudaFree(b->d_segs);
+        b->d_segs = nullptr;
+        const size_t cap = std::max<size_t>(segs.size(), 1);
+        BCUDA(cudaMalloc((void**)&b->d_segs, cap * sizeof(int4)));
+        b->segs_cap = cap;
     }
-    BCUDA(cudaMemcpyAsync(b->d_insts, insts.data(), insts.size() * sizeof(BatchInst), cudaMemcpyHostToDevice,
+    BCUDA(cudaMemcpyAsync(b->d_insts, insts.data(), insts.size() * sizeof(PInst), cudaMemcpyHostToDevice,
                           b->stream));
-    if (!tiles.empty())
-        BCUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice,
+    if (!segs.empty())
+        BCUDA(cudaMemcpyAsync(b->d_segs, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice,
                               b->stream));
     // the host vectors die here: wait for the copies
     BCUDA(cudaStreamSynchronize(b->stream));
-    b->ntiles = (int)tiles.size();
+    b->nsegs = (int)segs.size();
+    b->pinned_seg = b->seg_tiles;
     b->dirty = false;
     return LBM_OK;
 }
 
+// One run of the persistent kernel: a graph of two nodes, the reset of the work-item counter and
+// the kernel, built once per grid size; later runs only update the kernel's arguments.
 int launch(lbm_batch* b, int grid, long long step0, int nsteps) {
-    b->a_insts = b->d_insts;
-    b->a_tiles = b->d_tiles;
-    b->a_ntiles = b->ntiles;
-    b->a_step0 = step0;
-    b->a_nsteps = nsteps;
-    b->a_bar = GridBarrier{b->d_bar, b->d_bar + 1, b->d_err, b->bar_limit};
-    void* args[] = {(void*)&b->a_insts, (void*)&b->a_tiles, (void*)&b->a_ntiles, (void*)&b->a_step0,
-                    (void*)&b->a_nsteps, (void*)&b->a_bar};
+    b->a_args = PbArgs{b->d_insts, b->d_segs, b->nsegs, nsteps, step0, b->d_queue, 0ull, b->d_err, b->wait_limit};
+    void* args[] = {(void*)&b->a_args};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(b->kernel);
+    kp.func = const_cast<void*>(b->kernel.func);
     kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(b->bx, b->by);
-    kp.sharedMemBytes = 0;
+    kp.blockDim = b->kernel.block;
+    kp.sharedMemBytes = (unsigned)b->kernel.smem;
     kp.kernelParams = args;
     kp.extra = nullptr;
     if (b->use_graph) {
         cudaError_t e = cudaSuccess;
         if (!b->exec || b->graph_grid != grid) {
             free_graph(b);
+            cudaGraphNode_t reset = nullptr;
+            cudaMemsetParams mp{};
+            mp.dst = b->d_queue;
+            mp.value = 0;
+            mp.elementSize = 4;
+            mp.width = 2;   // the 64-bit counter as two 32-bit words
+            mp.height = 1;
+            mp.pitch = 0;
             e = cudaGraphCreate(&b->graph, 0);
-            if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->node, b->graph, nullptr, 0, &kp);
-            if (e == cudaSuccess) {
-                cudaLaunchAttributeValue v{};
-                v.cooperative = 1;
-                e = cudaGraphKernelNodeSetAttribute(b->node, cudaLaunchAttributeCooperative, &v);
-            }
+            if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&reset, b->graph, nullptr, 0, &mp);
+            if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->node, b->graph, &reset, 1, &kp);
             if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
             if (e == cudaSuccess) b->graph_grid = grid;
         } else {
@@ -202,22 +239,33 @@ int launch(lbm_batch* b, int grid, long long step0, int nsteps) {
         }
         if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
         if (e == cudaSuccess) return LBM_OK;
-        // graphs with cooperative nodes unavailable: launch directly from now on
+        // graphs unavailable: launch directly from now on
         cudaGetLastError();
         free_graph(b);
         b->use_graph = false;
     }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(b->bx, b->by);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = b->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    BCUDA(cudaLaunchKernelExC(&cfg, b->kernel, args));
+    BCUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream));
+    BCUDA(cudaLaunchKernel(b->kernel.func, dim3(grid), b->kernel.block, args, (size_t)b->kernel.smem, b->stream));
+    return LBM_OK;
+}
+
+// Choose the persistent kernel of the batch's class (16-bit storage: staged tiles; else plain).
+int choose_kernel(lbm_batch* b, int path) {
+    if (path < 0) path = (b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16) ? PB_STAGED : PB_PLAIN;
+    const PbKernel k = find_pbatch_kernel(b->Q, b->storage, b->collision, path);
+    if (!k.func) return set_error(LBM_EINVAL, "no persistent kernel of path %d for this lattice/storage/collision", path);
+    if (k.smem > 0)
+        BCUDA(cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem));
+    int per_sm = 0, sms = 0;
+    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, (int)(k.block.x * k.block.y), k.smem));
+    BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    if (per_sm < 1) return set_error(LBM_ECUDA, "the persistent kernel does not fit on an SM");
+    b->kernel = k;
+    b->path = path;
+    b->bx = k.tile_x;
+    b->by = k.tile_y;
+    b->max_blocks = per_sm * sms;
+    free_graph(b);
     return LBM_OK;
 }
 
@@ -233,15 +281,11 @@ int lbm_batch_create(int lattice, int storage, int collision, size_t device_budg
     if (!host_lattice(lattice, H)) return set_error(LBM_EINVAL, "lattice must be LBM_D2Q9 or LBM_D2Q37");
     if (!storage_size(storage)) return set_error(LBM_EINVAL, "bad storage type %d", storage);
     if (collision != LBM_COLL_BGK && collision != LBM_COLL_REGULARIZED) return set_error(LBM_EINVAL, "bad collision");
-    BatchKernelFn k = find_batch_kernel(lattice, storage, collision);
-    if (!k) return set_error(LBM_EINVAL, "no batch kernel for this lattice/storage/collision");
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return set_error(LBM_ENOMEM, "host allocation");
     b->Q = lattice;
     b->storage = storage;
     b->collision = collision;
-    b->kernel = k;
-    int rc = LBM_OK;
     auto fail = [&](int code) {
         lbm_batch_destroy(b);
         return code;
@@ -254,23 +298,17 @@ int lbm_batch_create(int lattice, int storage, int collision, size_t device_budg
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(set_error(LBM_ECUDA, "stream creation"));
     b->own_stream = true;
-    if (cudaMalloc((void**)&b->d_bar, 2 * sizeof(unsigned int)) != cudaSuccess ||
+    if (cudaMalloc((void**)&b->d_queue, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void**)&b->d_err, sizeof(int)) != cudaSuccess ||
-        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(b->d_queue, 0, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess)
-        return fail(set_error(LBM_ENOMEM, "batch barrier"));
+        return fail(set_error(LBM_ENOMEM, "batch work counter"));
     for (int k = 0; k < kSubStreams; ++k)
         if (cudaStreamCreateWithFlags(&b->sub[k], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
             return fail(set_error(LBM_ECUDA, "stream creation"));
     if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return fail(set_error(LBM_ECUDA, "event creation"));
-    int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->kernel, b->bx * b->by, 0) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || per_sm < 1)
-        return fail(set_error(LBM_ECUDA, "occupancy query of the batch kernel"));
-    b->max_blocks = per_sm * sms;
-    (void)rc;
     *out = b;
     return LBM_OK;
 }
@@ -296,6 +334,7 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
         return set_error(LBM_EINVAL, "the persistent batch kernel is built for bounce-back walls only");
     if (b->mode == LBM_BATCH_PERSISTENT && d->geom.layout != LBM_LAYOUT_AB)
         return set_error(LBM_EINVAL, "the persistent batch kernel runs the two-buffer layout only");
+    if (b->mode == LBM_BATCH_PERSISTENT && !b->kernel.func && (rc = choose_kernel(b, -1))) return rc;
     HostLattice H;
     host_lattice(d->lattice, H);
     const size_t bytes = footprint(H, d->nx, d->ny, d->geom.storage, d->geom.layout, d->nsteps, b->bx, b->by);
@@ -315,42 +354,47 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     if (id < 0) id = (int)b->slots.size();
     // kernel shape, history and stream, on the instance's own stream first, so that adding an
     // instance does not wait for a run of the batch that may be in flight
-    if (b->mode == LBM_BATCH_PERSISTENT) sim_disable_stream_offset(sim);  // the kernel reads fixed params
-    // default kernels, fastest measured in this mode: for D2Q37, the staged kernel with three rows
-    // per thread (27) for 16-bit storage and the plain kernel with 7 resident blocks per SM (2) for
-    // FP32; 16-bit D2Q9 takes the staged kernel 10; else the plain kernel
     const bool half = b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16;
-    const int want = b->variant >= 0 ? b->variant
-                     : half ? (b->Q == 37 ? 27 : 10)
-                     : (b->Q == 37 && b->storage == LBM_STORE_F32) ? 2 : 0;
-    if (b->mode == LBM_BATCH_PERSISTENT || want == 0 || lbm_set_variant(sim, want) != LBM_OK)
-        rc = lbm_set_tile(sim, b->bx, b->by);
+    if (b->mode == LBM_BATCH_PERSISTENT) {
+        // the instance's tile shape is the persistent kernel's: staged 64 x 3 tiles (variant 27:
+        // its load boxes and tile slots) or plain 32 x 4 tiles
+        if (b->path == PB_STAGED) rc = lbm_set_variant(sim, 27);
+        else if (b->Q == 37 && b->storage != LBM_STORE_F64) rc = lbm_set_variant(sim, 2);
+        else rc = lbm_set_tile(sim, 32, 4);
+    } else {
+        // default kernels, fastest measured in this mode: for D2Q37, the staged kernel with three
+        // rows per thread (27) for 16-bit storage and the plain kernel with 7 resident blocks per SM
+        // (2) for FP32; 16-bit D2Q9 takes the staged kernel 10; else the plain kernel
+        const int want = b->variant >= 0 ? b->variant
+                         : half ? (b->Q == 37 ? 27 : 10)
+                         : (b->Q == 37 && b->storage == LBM_STORE_F32) ? 2 : 0;
+        if (want == 0 || lbm_set_variant(sim, want) != LBM_OK) rc = lbm_set_tile(sim, b->bx, b->by);
+    }
     if (rc) return undo(rc);
     clear_error();
     // (+1: an in-place even step also writes the force of the step after it)
     if ((rc = sim_reserve(sim, (size_t)d->nsteps + 1))) return undo(rc);
     if ((rc = lbm_set_stream(sim, b->mode == LBM_BATCH_STREAMS ? b->sub[id % kSubStreams] : b->stream)))
         return undo(rc);
-    // drive table: nsteps doubles followed by the same values as nsteps floats
-    const size_t N = (size_t)d->nsteps;
-    std::vector<double> table(N + (N + 1) / 2, 0.0);
-    float* tf = reinterpret_cast<float*>(table.data() + N);
-    for (size_t n = 0; n < N; ++n) {
-        table[n] = drive_value(d->geom.drive, d->geom.u0, d->omega, (long)n);
-        tf[n] = (float)table[n];
-    }
-    double* drv = nullptr;
-    if (cudaMalloc((void**)&drv, table.size() * sizeof(double)) != cudaSuccess)
-        return undo(set_error(LBM_ENOMEM, "drive table"));
-    if (cudaMemcpy(drv, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(drv);
-        return undo(set_error(LBM_ECUDA, "drive table upload"));
-    }
     Slot s;
+    if (b->mode == LBM_BATCH_PERSISTENT) {
+        // per-step constants, tile counters (0: no step done) and the force ring (entry j free,
+        // as if the step j - kRing had left it)
+        const SimView v = sim_view(sim);
+        const size_t pb = pb_layout(d->nsteps, (v.ny + v.by - 1) / v.by, v.nslots, &s);
+        std::vector<unsigned char> host(pb, 0);
+        sim_step_constants(sim, d->nsteps, reinterpret_cast<StepConst*>(host.data()));
+        int* fin = reinterpret_cast<int*>(host.data() + s.off_fin);
+        for (int j = 0; j < kRing; ++j) fin[j] = j - kRing + 1;
+        if (cudaMalloc((void**)&s.d_pb, pb) != cudaSuccess) return undo(set_error(LBM_ENOMEM, "batch step table"));
+        if (cudaMemcpy(s.d_pb, host.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(s.d_pb);
+            return undo(set_error(LBM_ECUDA, "batch step table upload"));
+        }
+    }
     s.sim = sim;
     s.start = b->gstep;
     s.nsteps = d->nsteps;
-    s.d_drive = drv;
     s.bytes = bytes;
     if (id == (int)b->slots.size()) b->slots.push_back(s);
     else b->slots[id] = s;
@@ -368,7 +412,7 @@ int lbm_batch_run(lbm_batch* b, long steps) {
     if (steps > (1l << 30)) return set_error(LBM_EINVAL, "too many steps in one run");
     // drop instances that finished before this run
     for (const Slot& s : b->slots)
-        if (slot_live(s) && !slot_running(b, s) && b->ntiles > 0) b->dirty = true;
+        if (slot_live(s) && !slot_running(b, s) && b->nsegs > 0) b->dirty = true;
     if (b->mode == LBM_BATCH_STREAMS) {
         // every running instance advances on its own stream chain; the sub-streams follow the
         // batch stream's earlier work and the batch stream waits for theirs at the end
@@ -394,9 +438,9 @@ int lbm_batch_run(lbm_batch* b, long steps) {
     if (b->dirty && (rc = rebuild(b))) return rc;
     bool any = false;
     for (const Slot& s : b->slots) any = any || slot_running(b, s);
-    if (any && b->ntiles > 0) {
-        const int grid = std::min(b->ntiles, b->max_blocks);
-        BCUDA(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
+    if (any && b->nsegs > 0) {
+        const long long items = (long long)b->nsegs * steps;
+        const int grid = (int)std::min<long long>(items, b->max_blocks);
         if ((rc = launch(b, grid, b->gstep, (int)steps))) return rc;
         ++b->launches;
     }
@@ -422,7 +466,8 @@ int lbm_batch_synchronize(lbm_batch* b) {
         if (slot_live(s) && (rc = lbm_synchronize(s.sim)) != LBM_OK) return rc;
     int err = 0;
     BCUDA(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err & 2) return set_error(LBM_ETIMEOUT, "a grid-barrier wait of the batch kernel timed out; states are undefined");
+    if (err & 8)
+        return set_error(LBM_ETIMEOUT, "a bounded wait of the persistent batch kernel ran out; states are undefined");
     return LBM_OK;
 }
 
@@ -451,7 +496,7 @@ int lbm_batch_remove(lbm_batch* b, int slot) {
     for (int k = 0; k < kSubStreams; ++k) BCUDA(cudaStreamSynchronize(b->sub[k]));
     Slot& s = b->slots[slot];
     lbm_destroy(s.sim);
-    cudaFree(s.d_drive);
+    cudaFree(s.d_pb);
     b->used -= s.bytes;
     s = Slot();
     b->dirty = true;
@@ -462,7 +507,7 @@ int lbm_batch_set_barrier_limit(lbm_batch* b, long long cycles) {
     int rc = check_batch(b);
     if (rc) return rc;
     if (cycles < 0) return set_error(LBM_EINVAL, "negative limit");
-    b->bar_limit = cycles;
+    b->wait_limit = cycles;
     return LBM_OK;
 }
 
@@ -518,7 +563,27 @@ int lbm_batch_set_mode(lbm_batch* b, int mode) {
     if (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_STREAMS) return set_error(LBM_EINVAL, "bad batch mode");
     for (const Slot& s : b->slots)
         if (slot_live(s)) return set_error(LBM_EINVAL, "set the mode before adding instances");
+    if (mode == LBM_BATCH_PERSISTENT) {
+        // the persistent kernel: staged tiles for variant 27, plain tiles for 0 or 2, the class's
+        // default otherwise
+        const int path = b->variant == 27 ? PB_STAGED : (b->variant == 0 || b->variant == 2) ? PB_PLAIN : -1;
+        if ((rc = choose_kernel(b, path))) return rc;
+    } else {
+        b->bx = 32;
+        b->by = 4;
+    }
     b->mode = mode;
+    return LBM_OK;
+}
+
+int lbm_batch_set_segment(lbm_batch* b, int tiles) {
+    int rc = check_batch(b);
+    if (rc) return rc;
+    if (tiles < 1 || tiles > 1024) return set_error(LBM_EINVAL, "segment of %d tiles: need 1..1024", tiles);
+    // the row counters count segments, so the length is fixed once the persistent kernel has run
+    if (b->pinned_seg && tiles != b->pinned_seg)
+        return set_error(LBM_EINVAL, "the segment length is fixed after the first persistent run");
+    b->seg_tiles = tiles;
     return LBM_OK;
 }
 
@@ -526,6 +591,14 @@ int lbm_batch_set_variant(lbm_batch* b, int variant) {
     int rc = check_batch(b);
     if (rc) return rc;
     if (variant < -1) return set_error(LBM_EINVAL, "bad variant %d", variant);
+    if (b->mode == LBM_BATCH_PERSISTENT) {
+        for (const Slot& s : b->slots)
+            if (slot_live(s)) return set_error(LBM_EINVAL, "set the persistent kernel before adding instances");
+        const int path = variant == 27 ? PB_STAGED : (variant == 0 || variant == 2) ? PB_PLAIN : -1;
+        if (variant >= 0 && path < 0)
+            return set_error(LBM_EINVAL, "the persistent kernel runs variant 27 (staged) or 0/2 (plain), not %d", variant);
+        if ((rc = choose_kernel(b, path))) return rc;
+    }
     b->variant = variant;
     return LBM_OK;
 }
@@ -536,7 +609,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (Slot& s : b->slots) {
         if (s.sim) lbm_destroy(s.sim);
-        cudaFree(s.d_drive);
+        cudaFree(s.d_pb);
     }
     for (int k = 0; k < kSubStreams; ++k) {
         if (b->sub[k]) {
@@ -548,8 +621,8 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     free_graph(b);
     cudaFree(b->d_insts);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_bar);
+    cudaFree(b->d_segs);
+    cudaFree(b->d_queue);
     cudaFree(b->d_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -19,7 +19,7 @@
 
 #include "lbm.h"
 #include "runtime.h"
-#include "step_tma.cuh"
+#include "pbatch.cuh"
 
 namespace lbm {
 
@@ -28,7 +28,8 @@ void tma_box_q9(int storage, int bx, int* bw, int* pad);
 
 // D2Q37 launch tables, one translation unit per storage type (step_q37_inst.cuh).
 #define LBM_Q37_DECLS(SFX)                                          \
-    void* find_launcher_q37_##SFX(int coll, bool batched);          \
+    void* find_launcher_q37_##SFX(int coll);                        \
+    PbKernel find_pbatch_q37_##SFX(int coll, int path);             \
     void* find_launcher_q37_##SFX##_ds(int coll);                   \
     void* find_occ_launcher_q37_##SFX(int coll, int variant);       \
     void* find_tma_launcher_q37_##SFX(int coll, int variant);       \
@@ -40,7 +41,8 @@ LBM_Q37_DECLS(f16)
 #undef LBM_Q37_DECLS
 
 struct Q37Table {
-    void* (*plain)(int coll, bool batched);
+    void* (*plain)(int coll);
+    PbKernel (*pbatch)(int coll, int path);
     void* (*plain_ds)(int coll);
     void* (*occ)(int coll, int variant);
     void* (*tma)(int coll, int variant);
@@ -49,7 +51,7 @@ struct Q37Table {
 
 static const Q37Table* q37_table(int storage) {
 #define LBM_Q37_ROW(SFX)                                                                          \
-    {find_launcher_q37_##SFX, find_launcher_q37_##SFX##_ds, find_occ_launcher_q37_##SFX,          \
+    {find_launcher_q37_##SFX, find_pbatch_q37_##SFX, find_launcher_q37_##SFX##_ds, find_occ_launcher_q37_##SFX, \
      find_tma_launcher_q37_##SFX, tma_box_q37_##SFX}
     static const Q37Table rows[4] = {LBM_Q37_ROW(f64), LBM_Q37_ROW(f32), LBM_Q37_ROW(bf16), LBM_Q37_ROW(f16)};
 #undef LBM_Q37_ROW
@@ -121,12 +123,13 @@ static int encode_map(CUtensorMap* map, void* base, int storage, int nx, int ny,
     return LBM_OK;
 }
 
-void* find_launcher_q9(int storage, int coll, bool batched);
+void* find_launcher_q9(int storage, int coll);
 void* find_launcher_q9_ds(int storage, int coll);
+PbKernel find_pbatch_q9(int storage, int coll, int path);
 
-static void* find_launcher(int Q, int storage, int coll, bool batched) {
-    if (Q == 9) return find_launcher_q9(storage, coll, batched);
-    if (Q == 37 && q37_table(storage)) return q37_table(storage)->plain(coll, batched);
+static void* find_launcher(int Q, int storage, int coll) {
+    if (Q == 9) return find_launcher_q9(storage, coll);
+    if (Q == 37 && q37_table(storage)) return q37_table(storage)->plain(coll);
     return nullptr;
 }
 
@@ -155,14 +158,16 @@ StepLaunchFn find_aa_launcher(int Q, int storage, int coll, int phase) {
 }
 
 StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall) {
-    if (wall == 0) return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll, false));
+    if (wall == 0) return reinterpret_cast<StepLaunchFn>(find_launcher(Q, storage, coll));
     void* f = nullptr;
     if (Q == 9) f = find_launcher_q9_ds(storage, coll);
     else if (Q == 37 && q37_table(storage)) f = q37_table(storage)->plain_ds(coll);
     return reinterpret_cast<StepLaunchFn>(f);
 }
-BatchKernelFn find_batch_kernel(int Q, int storage, int coll) {
-    return find_launcher(Q, storage, coll, true);
+PbKernel find_pbatch_kernel(int Q, int storage, int coll, int path) {
+    if (Q == 9) return find_pbatch_q9(storage, coll, path);
+    if (Q == 37 && q37_table(storage)) return q37_table(storage)->pbatch(coll, path);
+    return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -608,6 +613,9 @@ SimView sim_view(const lbm_sim* s) {
     v.esize = s->esize;
     v.n_fluid = s->n_fluid;
     v.aa = s->aa ? 1 : 0;
+    v.variant = s->variant;
+    v.ntiles = s->ntiles;
+    v.maps = s->maps;
     return v;
 }
 
@@ -619,8 +627,27 @@ void sim_disable_stream_offset(lbm_sim* s) {
 }
 
 void sim_advance(lbm_sim* s, long steps) {
+    if (s->stream_off)
+        for (long k = 0; k < steps; ++k) s->U_stream += drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done + k);
     s->steps_done += steps;
     s->cur ^= (int)(steps & 1);
+}
+
+void sim_step_constants(const lbm_sim* s, long count, StepConst* out) {
+    double U = s->U_stream;
+    for (long k = 0; k < count; ++k) {
+        StepConst& c = out[k];
+        std::memset(&c, 0, sizeof(c));
+        c.dv = drive_value(s->geom.drive, s->geom.u0, s->omega, s->steps_done + k);
+        c.dv_f = (float)c.dv;
+        if (s->stream_off) {
+            float* H = c.H;  // HM[6], Hl[7], Hs[7], He[4], Ho[4]
+            stream_offset_cx(s, U, H + 6, H);
+            stream_offset_cx(s, U + c.dv, H + 13, nullptr);
+            stream_offset_eo(H + 13, H + 20, H + 24);
+            U += c.dv;
+        }
+    }
 }
 
 }  // namespace lbm
@@ -841,6 +868,7 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.reg_a_f = (float)d.reg_a;
     d.src_k_f = (float)d.src_k;
     s->stream_off = es == 2 && g.drive == LBM_DRIVE_BODYFORCE;
+    d.stream_off = s->stream_off ? 1 : 0;
     // default kernel on the default 32 x 4 tile: the fastest measured single-instance form, the
     // plain kernel with an occupancy floor (variant 1 for FP32, 2 for 16-bit storage)
     if (!s->aa && g.wall_scheme == LBM_SCHEME_BOUNCEBACK) {
@@ -1198,6 +1226,7 @@ int lbm_info(lbm_sim* s, lbm_info_t* o) {
     o->d2h_bytes = s->d2h_bytes;
     o->variant = s->variant;
     o->layout = s->aa ? LBM_LAYOUT_AA : LBM_LAYOUT_AB;
+    o->force_1e4 = s->geom.storage == LBM_STORE_BF16 ? 0 : 1;
     return LBM_OK;
 }
 

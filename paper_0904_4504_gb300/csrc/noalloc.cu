@@ -28,21 +28,26 @@ constexpr size_t kScratchBytes = kPartialBytes + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-void* g_addr[kMaxDevices] = {};
-cudaError_t g_addr_rc[kMaxDevices] = {};
+std::mutex g_addr_mutex;
+void* g_addr[kMaxDevices] = {};  // null until a lookup on that device has succeeded
 
-// Device address of the scratch array on `device` (looked up once, with that device current; the
-// name g_noalloc_scratch in host code is only a host-side stand-in, never a device address).
+// Device address of the scratch array on `device` (looked up with that device current; the name
+// g_noalloc_scratch in host code is only a host-side stand-in, never a device address).  Only a
+// successful lookup is kept: a failed one (say, inside a stream capture) is retried by the next call.
 cudaError_t scratch_address(int device, void** out) {
-    std::call_once(g_once[device], [device]() {
+    std::lock_guard<std::mutex> lock(g_addr_mutex);
+    if (!g_addr[device]) {
         void* p = nullptr;
-        cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        g_addr_rc[device] = rc;
-        g_addr[device] = rc == cudaSuccess ? p : nullptr;
-    });
+        const cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (rc != cudaSuccess) {
+            cudaGetLastError();  // the failure is reported through the return code, not left pending
+            *out = nullptr;
+            return rc;
+        }
+        g_addr[device] = p;
+    }
     *out = g_addr[device];
-    return g_addr_rc[device];
+    return cudaSuccess;
 }
 
 }  // namespace

@@ -1,13 +1,14 @@
 // runtime.h -- host-side helpers shared by the C-ABI translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <stddef.h>
 #include <stdint.h>
 
 #include <vector>
 
 #include "lbm.h"
-#include "step_kernel.cuh"
+#include "pbatch.cuh"
 
 namespace lbm {
 
@@ -51,6 +52,9 @@ struct SimView {
     double2* history;
     size_t esize, n_fluid;
     int aa;  // in-place single buffer (buf[1] is null)
+    int variant;
+    int ntiles;
+    const CUtensorMap* maps;  // staged variants: load boxes of buf[0], buf[1]
 };
 SimView sim_view(const lbm_sim* s);
 // Make room for `steps` entries of force history (may allocate).
@@ -59,5 +63,8 @@ int sim_reserve(lbm_sim* s, size_t steps);
 void sim_disable_stream_offset(lbm_sim* s);
 // Record that `steps` steps were run on the simulation's buffers by another launcher.
 void sim_advance(lbm_sim* s, long steps);
+// The per-step constants (drive, 16-bit stream offsets) of the simulation's next `count` steps,
+// exactly as lbm_step would set them.
+void sim_step_constants(const lbm_sim* s, long count, StepConst* out);
 
 }  // namespace lbm

@@ -131,10 +131,19 @@ __device__ __forceinline__ float kconst<float>(double, float f) { return f; }
 template <class ST> struct StoreT;
 // Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
 // elements) with one access; rnd(v) is v rounded to the storage type (what a store and a load give).
+// ldc loads through L2 only (ld.global.cg), never from L1 or the read-only path (ld.global.nc)
+// that the compiler may pick for a const __restrict__ pointer: the persistent batch kernel reads
+// populations that other blocks of the same launch wrote (made visible by an acquire), and an L1
+// line filled before that could still hold the old value.
 template <> struct StoreT<double> {
     using CT = double;
     static __device__ __forceinline__ double rnd(double v) { return v; }
     static __device__ __forceinline__ double ld(const double* p) { return *p; }
+    static __device__ __forceinline__ double ldc(const double* p) {
+        double v;
+        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
     static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
         const double2 v = *reinterpret_cast<const double2*>(p);
@@ -149,6 +158,11 @@ template <> struct StoreT<float> {
     using CT = float;
     static __device__ __forceinline__ float rnd(float v) { return v; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ float ldc(const float* p) {
+        float v;
+        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
     static __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
         const float2 v = *reinterpret_cast<const float2*>(p);
@@ -163,6 +177,11 @@ template <> struct StoreT<__nv_bfloat16> {
     using CT = float;
     static __device__ __forceinline__ float rnd(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float ldc(const __nv_bfloat16* p) {
+        unsigned short v;
+        asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+        return __bfloat162float(__ushort_as_bfloat16(v));
+    }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
         const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
@@ -177,6 +196,11 @@ template <> struct StoreT<__half> {
     using CT = float;
     static __device__ __forceinline__ float rnd(float v) { return __half2float(__float2half_rn(v)); }
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ float ldc(const __half* p) {
+        unsigned short v;
+        asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+        return __half2float(__ushort_as_half(v));
+    }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
         const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
@@ -189,7 +213,7 @@ template <> struct StoreT<__half> {
 };
 
 // Eq. 17 from global memory: h_i^adv(x) = h_i(x - c_i), periodic in x and y.
-template <class L, class ST>
+template <class L, class ST, bool COH = false>
 __device__ __forceinline__ void gather_global(const InstDev& P, const ST* __restrict__ src, int x, int y,
                                               typename StoreT<ST>::CT (&h)[L::Q]) {
     using S = StoreT<ST>;
@@ -211,7 +235,8 @@ __device__ __forceinline__ void gather_global(const InstDev& P, const ST* __rest
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of<L>(i), cy = cy_of<L>(i);
         // 32-bit element offset, widened once: one multiply-add per address
-        h[i] = S::ld(src + (unsigned)(i * plane + roff[cy + R] + col[cx + R]));
+        const ST* p = src + (unsigned)(i * plane + roff[cy + R] + col[cx + R]);
+        h[i] = COH ? S::ldc(p) : S::ld(p);
     }
 }
 
@@ -283,6 +308,10 @@ __device__ __forceinline__ void moments(SpDm&& spdm, T h0, T& m0, T& jx, T& jy, 
     }
 }
 
+// A product rounded on its own (never contracted with a later add into a fused multiply-add).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Collision coefficients of a node from its moments (storage units, relative to the stream offset
 // with 16-bit storage and the offset on): Eqs. 15 and 19 and the Guo-type source.  With 16-bit
 // storage the moments are scaled by s on the way in and the coefficients by 1/s on the way out.
@@ -298,8 +327,11 @@ __device__ __forceinline__ void coef_tail(const InstDev& P, double dv, float dv_
             m0 += (T)P.HM[0]; jx += (T)P.HM[1]; jy += (T)P.HM[2];
             pxx += (T)P.HM[3]; pxy += (T)P.HM[4]; pyy += (T)P.HM[5];
         }
+        // the storage scale is applied by rounded multiplies that the compiler may not fuse into
+        // a later add, so that every kernel variant computes the same bits
         const T s = kconst<T>(P.s, P.s_f);
-        m0 *= s; jx *= s; jy *= s; pxx *= s; pxy *= s; pyy *= s;
+        m0 = mul_rn(m0, s); jx = mul_rn(jx, s); jy = mul_rn(jy, s);
+        pxx = mul_rn(pxx, s); pxy = mul_rn(pxy, s); pyy = mul_rn(pyy, s);
     }
     constexpr double TH = L::theta();
     const T th = (T)TH, ith = (T)(1.0 / TH);
@@ -349,9 +381,11 @@ __device__ __forceinline__ void coef_tail(const InstDev& P, double dv, float dv_
     if (SCALED) {
         // outputs are wanted in storage units (divided by s): scale the coefficients once per node
         const T is = kconst<T>(P.inv_s, P.inv_s_f);
-        C.c0 *= is; C.e1 *= is; C.e2 *= is; C.o0 *= is; C.o1 *= is;
-        C.rxx *= is; C.rxy *= is; C.ryy *= is; C.kf *= is; C.hf *= is;
-        C.e0 *= is; C.kfu *= is;
+        C.c0 = mul_rn(C.c0, is); C.e1 = mul_rn(C.e1, is); C.e2 = mul_rn(C.e2, is);
+        C.o0 = mul_rn(C.o0, is); C.o1 = mul_rn(C.o1, is);
+        C.rxx = mul_rn(C.rxx, is); C.rxy = mul_rn(C.rxy, is); C.ryy = mul_rn(C.ryy, is);
+        C.kf = mul_rn(C.kf, is); C.hf = mul_rn(C.hf, is);
+        C.e0 = mul_rn(C.e0, is); C.kfu = mul_rn(C.kfu, is);
     }
     // constant parts of the outputs per m = |c_x|; 16-bit storage subtracts the stream offset of
     // the stored state here, once per node (He, Ho are zero when it is off)
@@ -368,7 +402,7 @@ __device__ __forceinline__ void coef_tail(const InstDev& P, double dv, float dv_
 // term 2 w_i rho0 c_i.U_w / theta (w_i and s divided out); adds the momentum the node's body links
 // hand to the body to (Fx, Fy).  With 16-bit storage and the stream offset on, h holds values
 // relative to the stream on entry and exit for the regularized collision, absolute ones for BGK.
-template <class L, class ST, int COLL, int OWN>
+template <class L, class ST, int COLL, int OWN, bool COH = false>
 __device__ __forceinline__ void bb_fixup(const InstDev& P, const ST* __restrict__ src, int idx, double dv,
                                          typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy) {
     using S = StoreT<ST>;
@@ -381,7 +415,8 @@ __device__ __forceinline__ void bb_fixup(const InstDev& P, const ST* __restrict_
     for (int i = 1; i < L::Q; ++i) {
         if ((blk >> i) & 1ull) {
             const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-            T own = S::ld(src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx);
+            const ST* po = src + (OWN == OWN_SWAPPED ? i : opp_of<L>(i)) * plane + idx;
+            T own = COH ? S::ldc(po) : S::ld(po);
             if (off) own += (T)off_l<L>(P, opp_of<L>(i));
             double mw = 0.0;
             if ((lk.x >> i) & 1ull) {
@@ -399,7 +434,7 @@ __device__ __forceinline__ void bb_fixup(const InstDev& P, const ST* __restrict_
     }
 }
 
-template <class L, class ST, int COLL, int WALL = 0, int OWN = OWN_OPP>
+template <class L, class ST, int COLL, int WALL = 0, int OWN = OWN_OPP, bool COH = false>
 __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                         float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
                                         Coef<typename StoreT<ST>::CT>& C) {
@@ -419,7 +454,7 @@ __device__ __forceinline__ void prepare(const InstDev& P, const void* src_v, int
         for (int i = 0; i < Q; ++i) h[i] += (T)off_l<L>(P, i);
     }
     if (cls == NODE_BOUNDARY && WALL == 0 && OWN != OWN_NONE) {
-        bb_fixup<L, ST, COLL, OWN>(P, src, idx, dv, h, Fx, Fy);
+        bb_fixup<L, ST, COLL, OWN, COH>(P, src, idx, dv, h, Fx, Fy);
     } else if (WALL == 1 && cls == NODE_BOUNDARY && OWN == OWN_OPP) {
         // Eq. 11 on blocked links: each wall returns its discrete Maxwellian at the wall velocity,
         // f_i = w_i rho_w (1 + e_i(U_w)), with rho_w set so that the node gets back exactly the mass
@@ -642,17 +677,17 @@ __device__ __forceinline__ void emit_outputs(const Coef<typename StoreT<ST>::CT>
 }
 
 // prepare + evaluation of one node (see emit_outputs).
-template <class L, class ST, int COLL, int WALL = 0, class Emit>
+template <class L, class ST, int COLL, int WALL = 0, bool COH = false, class Emit>
 __device__ __forceinline__ void collide_emit(const InstDev& P, const void* src_v, int x, int y, int cls, double dv,
                                              float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx, double& Fy,
                                              Emit&& emit) {
     Coef<typename StoreT<ST>::CT> C;
-    prepare<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
+    prepare<L, ST, COLL, WALL, OWN_OPP, COH>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy, C);
     emit_outputs<L, ST, COLL>(C, h, emit);
 }
 
 // prepare + evaluation + store of one node.
-template <class L, class ST, int COLL, int WALL = 0>
+template <class L, class ST, int COLL, int WALL = 0, bool COH = false>
 __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_v, void* dst_v, int x, int y, int cls,
                                               double dv, float dv_f, typename StoreT<ST>::CT (&h)[L::Q], double& Fx,
                                               double& Fy) {
@@ -662,8 +697,8 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     // pointer plus stride * i, one widening multiply-add
     ST* __restrict__ dst = static_cast<ST*>(dst_v) + (y * P.pitch + x);
     const unsigned plane = (unsigned)P.plane;
-    collide_emit<L, ST, COLL, WALL>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy,
-                                    [&](int i, T v) { S::st(dst + (unsigned long long)plane * (unsigned)i, v); });
+    collide_emit<L, ST, COLL, WALL, COH>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy,
+                                         [&](int i, T v) { S::st(dst + (unsigned long long)plane * (unsigned)i, v); });
 }
 
 // Advection + wall + collision of the fluid node (x, y), sources from global memory.  WALL selects
@@ -678,10 +713,11 @@ __device__ __forceinline__ void node_update(const InstDev& P, const void* src, v
 }
 
 // Force partial of a tile (fixed-order reduction); the last tile with body links to finish sums
-// the slots in a fixed order, adds the constant part and writes the force of the step.
+// the slots in a fixed order, adds the constant part and writes the force of the step.  Returns
+// true (block-uniform) in the block that wrote the force.
 template <int NF>
-__device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int slot, double2* force_out, double (&F)[2 * NF]) {
-    if (slot < 0) return;  // block-uniform: no body link in this tile
+__device__ __forceinline__ bool tile_epilogue_n(const InstDev& P, int slot, double2* force_out, double (&F)[2 * NF]) {
+    if (slot < 0) return false;  // block-uniform: no body link in this tile
     __shared__ double2 red[32 * NF];
     __shared__ int last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -737,11 +773,12 @@ __device__ __forceinline__ void tile_epilogue_n(const InstDev& P, int slot, doub
         }
         if (tid == 0) *P.ticket = 0u;
     }
+    return last != 0;
 }
 
-__device__ __forceinline__ void tile_epilogue(const InstDev& P, int slot, double2* force_out, double Fx, double Fy) {
+__device__ __forceinline__ bool tile_epilogue(const InstDev& P, int slot, double2* force_out, double Fx, double Fy) {
     double F[2] = {Fx, Fy};
-    tile_epilogue_n<1>(P, slot, force_out, F);
+    return tile_epilogue_n<1>(P, slot, force_out, F);
 }
 
 // Node (x, y) inside the grid, of class cls (already loaded).  With 4- and 8-byte storage its pulls
@@ -788,81 +825,7 @@ __global__ void __launch_bounds__(512) step_kernel(const __grid_constant__ InstD
     process_tile<L, ST, COLL, WALL, true>(P, blockIdx.x, P.src, P.dst, P.dv, P.dv_f, P.force_out);
 }
 
-// One instance of a batch: its step-kernel parameters plus what changes from step to step.
-struct BatchInst {
-    InstDev base;                // geometry, constants, force scratch (src/dst/dv/force_out unused)
-    const void* buf[2];          // population buffers; local step n reads buf[n & 1]
-    const double* drive;         // [nsteps] drive of each local step
-    const float* drive_f;        // [nsteps] the same in FP32
-    double2* history;            // [nsteps] force of each local step
-    long long start;             // batch step at which local step 0 runs
-    long long nsteps;            // local steps to run
-};
-
-// Grid-wide barrier of a cooperative launch with a bounded wait.  Returns false (and sets bit 1 of
-// *err) if this block gave up after `limit` clock cycles; a block that sees the error returns.
-struct GridBarrier {
-    unsigned int* count;         // blocks arrived at the current barrier
-    unsigned int* gen;           // barrier generation
-    int* err;                    // bit 1: a barrier wait timed out
-    long long limit;             // clock cycles a block waits before giving up
-};
-
-__device__ __forceinline__ bool grid_sync(const GridBarrier& B) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        volatile unsigned int* gen = B.gen;
-        const unsigned int g = *gen;
-        __threadfence();
-        int good = 1;
-        if (atomicAdd(B.count, 1u) == gridDim.x - 1) {
-            *B.count = 0u;
-            __threadfence();
-            atomicAdd(B.gen, 1u);
-        } else {
-            // the clock is checked before the flag, so a limit of 0 gives up at once
-            const long long t0 = clock64();
-            while (true) {
-                if (clock64() - t0 >= B.limit) {
-                    atomicOr(B.err, 2);
-                    good = 0;
-                    break;
-                }
-                if (*gen != g) break;
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        if (good && (*(volatile int*)B.err & 2)) good = 0;
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// Persistent batched step: a cooperative grid walks the tiles of every instance (round robin) for
-// `nsteps` batch steps starting at batch step `step0`, with a grid barrier between steps.
-// Instances outside [start, start + nsteps) at a given step are skipped.
-template <class L, class ST, int COLL>
-__global__ void __launch_bounds__(128, 5) batch_kernel(const BatchInst* __restrict__ insts, const int2* __restrict__ tiles,
-                                                    int ntiles, long long step0, int nsteps, GridBarrier bar) {
-    for (int k = 0; k < nsteps; ++k) {
-        const long long gstep = step0 + k;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int2 tl = tiles[t];
-            const BatchInst& B = insts[tl.x];
-            const long long n = gstep - B.start;
-            if (n < 0 || n >= B.nsteps) continue;
-            process_tile<L, ST, COLL>(B.base, tl.y, B.buf[n & 1], const_cast<void*>(B.buf[(n + 1) & 1]),
-                                      B.drive[n], B.drive_f[n], B.history + n);
-        }
-        if (k + 1 < nsteps && !grid_sync(bar)) return;
-    }
-}
-
 using StepLaunchFn = cudaError_t (*)(const InstDev& P, dim3 block, cudaStream_t stream);
-using BatchKernelFn = const void*;
 
 template <class L, class ST, int COLL, int WALL = 0>
 cudaError_t launch_step(const InstDev& P, dim3 block, cudaStream_t stream) {
@@ -912,7 +875,5 @@ StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall = 0);
 // Plain step with an occupancy floor: variant 1 = 6 blocks of 128 per SM, 2 = 7; 3, 4 = 7 blocks with
 // 2 or 4 nodes per thread (nullptr if not built).
 StepLaunchFn find_occ_launcher(int Q, int storage, int coll, int variant);
-// Address of batch_kernel<...> for a cooperative launch (nullptr if not built).
-BatchKernelFn find_batch_kernel(int Q, int storage, int coll);
 
 }  // namespace lbm

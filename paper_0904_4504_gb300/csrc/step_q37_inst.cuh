@@ -3,18 +3,37 @@
 // compile in parallel).  Variant numbers are those of lbm_set_variant.
 #pragma once
 
-#include "step_tma.cuh"
+#include "pbatch.cuh"
 
 namespace lbm {
 
-// Plain step (or the persistent batch kernel), bounce-back walls.
+// Plain step, bounce-back walls.
 template <class ST>
-void* q37_plain(int coll, bool batched) {
-    if (coll == COLL_REG)
-        return batched ? (void*)&batch_kernel<D2Q37, ST, COLL_REG> : (void*)&launch_step<D2Q37, ST, COLL_REG>;
-    if (coll == COLL_BGK)
-        return batched ? (void*)&batch_kernel<D2Q37, ST, COLL_BGK> : (void*)&launch_step<D2Q37, ST, COLL_BGK>;
+void* q37_plain(int coll) {
+    if (coll == COLL_REG) return (void*)&launch_step<D2Q37, ST, COLL_REG>;
+    if (coll == COLL_BGK) return (void*)&launch_step<D2Q37, ST, COLL_BGK>;
     return nullptr;
+}
+
+// The persistent batch kernel (pbatch.cuh): staged 64 x 3 tiles (16-bit storage: 11 blocks of 64
+// threads per SM, the shape of variant 27; FP32: 6, as shared memory allows) or plain 32 x 4 tiles
+// (6 blocks of 128 threads per SM, the register budget of variant 1; FP64: 3).
+template <class ST, int COLL>
+PbKernel q37_pbatch_c(int path) {
+    constexpr bool wide = sizeof(ST) == 8;
+    if constexpr (!wide) {
+        if (path == PB_STAGED)
+            return pbatch_kernel_info<D2Q37, ST, COLL, PB_STAGED, 64, 3, sizeof(ST) == 2 ? 11 : 6>();
+    }
+    if (path == PB_PLAIN) return pbatch_kernel_info<D2Q37, ST, COLL, PB_PLAIN, 32, 4, wide ? 3 : 6>();
+    return PbKernel{nullptr, dim3(), 0, 0, 0};
+}
+
+template <class ST>
+PbKernel q37_pbatch(int coll, int path) {
+    if (coll == COLL_REG) return q37_pbatch_c<ST, COLL_REG>(path);
+    if (coll == COLL_BGK) return q37_pbatch_c<ST, COLL_BGK>(path);
+    return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
 // Plain step with diffuse-scattering walls.
@@ -83,7 +102,8 @@ void q37_box(int bx, int* bw, int* pad) {
 // The functions one translation unit exports for storage type ST under the suffix SFX.
 #define LBM_Q37_EXPORTS(SFX, ST, STAGED)                                                                 \
     namespace lbm {                                                                                      \
-    void* find_launcher_q37_##SFX(int coll, bool batched) { return q37_plain<ST>(coll, batched); }     \
+    void* find_launcher_q37_##SFX(int coll) { return q37_plain<ST>(coll); }                           \
+    PbKernel find_pbatch_q37_##SFX(int coll, int path) { return q37_pbatch<ST>(coll, path); }          \
     void* find_launcher_q37_##SFX##_ds(int coll) { return q37_plain_ds<ST>(coll); }                    \
     void* find_occ_launcher_q37_##SFX(int coll, int variant) {                                          \
         return STAGED ? q37_occ<ST>(coll, variant) : nullptr;                                            \

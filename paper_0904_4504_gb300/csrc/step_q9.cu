@@ -1,13 +1,13 @@
 // D2Q9 instantiations of the fused step (all storage types, both collisions).
-#include "step_tma.cuh"
+#include "pbatch.cuh"
 
 namespace lbm {
 
 #define LBM_CASE(ST_ENUM, ST, COLL)                                                            \
     case ST_ENUM * 2 + COLL:                                                                   \
-        return batched ? (void*)&batch_kernel<D2Q9, ST, COLL> : (void*)&launch_step<D2Q9, ST, COLL>;
+        return (void*)&launch_step<D2Q9, ST, COLL>;
 
-void* find_launcher_q9(int storage, int coll, bool batched) {
+void* find_launcher_q9(int storage, int coll) {
     switch (storage * 2 + coll) {
         LBM_CASE(ST_F64, double, COLL_BGK)
         LBM_CASE(ST_F64, double, COLL_REG)
@@ -19,6 +19,37 @@ void* find_launcher_q9(int storage, int coll, bool batched) {
         LBM_CASE(ST_F16, __half, COLL_REG)
         default:
             return nullptr;
+    }
+}
+
+#undef LBM_CASE
+
+// The persistent batch kernel (pbatch.cuh): staged 64 x 3 tiles (16-bit, FP32) or plain 32 x 4 tiles.
+template <class ST, int COLL>
+PbKernel q9_pbatch_c(int path) {
+    constexpr bool wide = sizeof(ST) == 8;
+    if constexpr (!wide) {
+        if (path == PB_STAGED)
+            return pbatch_kernel_info<D2Q9, ST, COLL, PB_STAGED, 64, 3, sizeof(ST) == 2 ? 16 : 12>();
+    }
+    if (path == PB_PLAIN) return pbatch_kernel_info<D2Q9, ST, COLL, PB_PLAIN, 32, 4, wide ? 6 : 8>();
+    return PbKernel{nullptr, dim3(), 0, 0, 0};
+}
+
+template <class ST>
+PbKernel q9_pbatch_s(int coll, int path) {
+    if (coll == COLL_REG) return q9_pbatch_c<ST, COLL_REG>(path);
+    if (coll == COLL_BGK) return q9_pbatch_c<ST, COLL_BGK>(path);
+    return PbKernel{nullptr, dim3(), 0, 0, 0};
+}
+
+PbKernel find_pbatch_q9(int storage, int coll, int path) {
+    switch (storage) {
+        case ST_F64: return q9_pbatch_s<double>(coll, path);
+        case ST_F32: return q9_pbatch_s<float>(coll, path);
+        case ST_BF16: return q9_pbatch_s<__nv_bfloat16>(coll, path);
+        case ST_F16: return q9_pbatch_s<__half>(coll, path);
+        default: return PbKernel{nullptr, dim3(), 0, 0, 0};
     }
 }
 
@@ -46,9 +77,9 @@ void* find_launcher_q9_ds(int storage, int coll) {
     }
 }
 
-// Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10, 11, 12 = one
-// node per thread on 32 x 4, 64 x 2, 64 x 4 tiles; 20, 21, 22 = two nodes per thread on 64 x 4,
-// 64 x 2, 128 x 2 tiles.
+// Launchers of the shared-memory-staged step, by variant (tiles in nodes): 10 = one node per
+// thread on 32 x 4 tiles; 20 = two nodes per thread on 64 x 4 tiles; 27 = 64 x 1 threads, three
+// rows each (64 x 3 tiles, the persistent batch kernel's staged shape).
 void* find_tma_launcher_q9(int storage, int coll, int variant) {
     if (variant < 0 || variant >= 32) return nullptr;
     switch ((storage * 2 + coll) * 32 + variant) {
@@ -76,6 +107,18 @@ void* find_tma_launcher_q9(int storage, int coll, int variant) {
             return (void*)&launch_step_tma1<D2Q9, __half, COLL_REG, 32, 4>;
         case (ST_F16 * 2 + COLL_REG) * 32 + 20:
             return (void*)&launch_step_pair<D2Q9, __half, COLL_REG, 32, 4>;
+        case (ST_F32 * 2 + COLL_BGK) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, float, COLL_BGK, 64, 1, 3, 12>;
+        case (ST_F32 * 2 + COLL_REG) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, float, COLL_REG, 64, 1, 3, 12>;
+        case (ST_BF16 * 2 + COLL_BGK) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, __nv_bfloat16, COLL_BGK, 64, 1, 3, 16>;
+        case (ST_BF16 * 2 + COLL_REG) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, __nv_bfloat16, COLL_REG, 64, 1, 3, 16>;
+        case (ST_F16 * 2 + COLL_BGK) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, __half, COLL_BGK, 64, 1, 3, 16>;
+        case (ST_F16 * 2 + COLL_REG) * 32 + 27:
+            return (void*)&launch_step_tman<D2Q9, __half, COLL_REG, 64, 1, 3, 16>;
         default:
             return nullptr;
     }

@@ -71,6 +71,7 @@ class lbm_info_t(ctypes.Structure):
         ("h2d_bytes", ctypes.c_size_t), ("d2h_bytes", ctypes.c_size_t),
         ("variant", ctypes.c_int),
         ("layout", ctypes.c_int),
+        ("force_1e4", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -198,6 +199,7 @@ def lib():
             "lbm_batch_set_barrier_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
             "lbm_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_batch_set_segment": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
             "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
             "lbm_batch_destroy": (None, [_P]),
@@ -444,6 +446,10 @@ def lbm_batch_set_mode(batch: int, mode: int) -> None:
 
 def lbm_batch_set_variant(batch: int, variant: int) -> None:
     _check(lib().lbm_batch_set_variant(batch, variant))
+
+
+def lbm_batch_set_segment(batch: int, tiles: int) -> None:
+    _check(lib().lbm_batch_set_segment(batch, tiles))
 
 
 def lbm_batch_set_barrier_limit(batch: int, cycles: int) -> None:

@@ -31,11 +31,19 @@ def _desc(Q, nx, ny, tau, omega, nsteps, storage=L.LBM_STORE_F32, coll=L.LBM_COL
 
 
 def batch_kernel_variant(d, mode=L.LBM_BATCH_STREAMS):
-    """The kernel a batch runs an instance with by default (lbm_batch_set_variant)."""
+    """The single-instance kernel that computes an instance as the batch does by default: in the
+    streams mode the kernel the batch launches (lbm_batch_set_variant); in the persistent mode the
+    kernel whose tile code and tile shape the persistent kernel runs (staged 64 x 3 tiles, variant
+    27, with 16-bit storage; plain 32 x 4 tiles otherwise, variant 2 where built)."""
     g = d.geom
-    if mode != L.LBM_BATCH_STREAMS or g.layout != L.LBM_LAYOUT_AB or g.wall_scheme != L.LBM_SCHEME_BOUNCEBACK:
+    if g.layout != L.LBM_LAYOUT_AB or g.wall_scheme != L.LBM_SCHEME_BOUNCEBACK:
         return 0
-    if g.storage in (L.LBM_STORE_BF16, L.LBM_STORE_F16):
+    half = g.storage in (L.LBM_STORE_BF16, L.LBM_STORE_F16)
+    if mode == L.LBM_BATCH_PERSISTENT:
+        if half:
+            return 27
+        return 2 if (d.lattice == 37 and g.storage != L.LBM_STORE_F64) else 0
+    if half:
         return 27 if d.lattice == 37 else 10
     return 2 if (d.lattice == 37 and g.storage == L.LBM_STORE_F32) else 0
 
@@ -69,10 +77,16 @@ MIX = [  # uneven sizes, parameters, geometries and lengths
 MODES = [L.LBM_BATCH_STREAMS, L.LBM_BATCH_PERSISTENT]
 
 
-@pytest.mark.parametrize("mode", MODES)
-def test_batch_equals_standalone_bitwise(mode):
-    descs = [_desc(37, nx, ny, tau, om, n, **kw) for nx, ny, tau, om, n, kw in MIX]
-    b = L.lbm_batch_create(37, L.LBM_STORE_F32, L.LBM_COLL_REGULARIZED)
+@pytest.mark.parametrize("Q,st", [(37, L.LBM_STORE_F32), (37, L.LBM_STORE_F16), (37, L.LBM_STORE_BF16),
+                                  (9, L.LBM_STORE_F16), (9, L.LBM_STORE_F32)],
+                         ids=["q37-f32", "q37-f16", "q37-bf16", "q9-f16", "q9-f32"])
+@pytest.mark.parametrize("mode", MODES, ids=["streams", "persistent"])
+def test_batch_equals_standalone_bitwise(mode, Q, st):
+    """Uneven instances (sizes, tau, omega, geometries, lengths, body-frame and lab-frame drives,
+    with 16-bit storage the stream offset on) in one batch give exactly the states and forces of
+    the same instances run alone with the kernel whose tile code the batch runs."""
+    descs = [_desc(Q, nx, ny, tau, om, n, storage=st, **kw) for nx, ny, tau, om, n, kw in MIX]
+    b = L.lbm_batch_create(Q, st, L.LBM_COLL_REGULARIZED)
     try:
         L.lbm_batch_set_mode(b, mode)
         slots = [L.lbm_batch_add(b, d) for d in descs]
@@ -225,3 +239,46 @@ def test_damping_sweep_matches_direct_fit():
     finally:
         L.lbm_destroy(h)
     assert rec["gamma_bar"] == direct and direct > 0
+
+
+@pytest.mark.parametrize("Q", [37, 9])
+@pytest.mark.parametrize("st", [L.LBM_STORE_BF16, L.LBM_STORE_F16], ids=["bf16", "f16"])
+@pytest.mark.parametrize("mode", MODES, ids=["streams", "persistent"])
+def test_batch_16bit_instances_match_oracle_step(mode, st, Q):
+    """16-bit storage in a batch (the mixed-precision form): after 9 batch steps, each instance's
+    10th step against one oracle step from the state it reached, with the bound of the 16-bit
+    parity tests (the exact step rounded once to the storage type, relative to |h| plus the stream
+    offset in the body frame).  Instances: a body-frame beam with interior (staged) tiles, a
+    lab-frame beam and a plate with its moving wall, of uneven sizes."""
+    from harness import g_to_oracle_state, stream_offset_magnitude
+    from test_gpu_parity import assert_force_close, assert_state_close
+
+    u0 = 2e-3
+    eq = 4 if Q == 37 else 2
+    cases = [(393, 90, 0.9, 0.05, dict(lx=23, ly=19)),
+             (140, 75, 1.3, 0.04, dict(lx=16, ly=24, drive=L.LBM_DRIVE_WALL)),
+             (96, 64, 0.7, 0.06, dict(kind=L.LBM_GEOM_PLATE, drive=L.LBM_DRIVE_WALL))]
+    b = L.lbm_batch_create(Q, st, L.LBM_COLL_REGULARIZED)
+    try:
+        L.lbm_batch_set_mode(b, mode)
+        descs = [_desc(Q, nx, ny, tau, om, 40, storage=st, u0=u0, **kw) for nx, ny, tau, om, kw in cases]
+        slots = [L.lbm_batch_add(b, d) for d in descs]
+        L.lbm_batch_run(b, 4)
+        L.lbm_batch_run(b, 5)
+        L.lbm_batch_synchronize(b)
+        g9 = [L.lbm_get_state(L.lbm_batch_instance(b, s)) for s in slots]
+        L.lbm_batch_run(b, 1)
+        L.lbm_batch_synchronize(b)
+        g10 = [L.lbm_get_state(L.lbm_batch_instance(b, s)) for s in slots]
+        F = [L.lbm_force_history(L.lbm_batch_instance(b, s)) for s in slots]
+    finally:
+        L.lbm_batch_destroy(b)
+    for d, a, z, Fh in zip(descs, g9, g10, F):
+        g = d.geom
+        lab = (orc.geometry_beam(d.nx, d.ny, g.lx, g.ly) if g.kind == L.LBM_GEOM_BEAM
+               else orc.geometry_plate(Q, d.nx, d.ny))
+        f, F_or = orc.run(Q, lab, d.tau, d.omega, u0, 1, eq_order=eq, collision=orc.COLL_REG, drive=g.drive,
+                          f=g_to_oracle_state(Q, a), n0=9, nthreads=orc.max_threads())
+        off = u0 * stream_offset_magnitude(Q, u0, d.omega, 10, eq) if g.drive == L.LBM_DRIVE_BODYFORCE else None
+        assert_state_close(Q, z, oracle_state_to_g(Q, f), lab, st, 1, a, off)
+        assert_force_close(Fh[9:10], F_or, Q, lab, st, 1)

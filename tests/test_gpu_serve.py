@@ -120,3 +120,39 @@ def test_in_place_layout_doubles_what_a_budget_admits():
     for (ra, ha), (rb, hb) in zip(out_aa, out_ab):
         amp = np.abs(hb[:, 0]).max()
         assert np.abs(ha[:, 0] - hb[:, 0]).max() <= 1e-5 * amp
+
+
+@pytest.mark.parametrize("Q,kind,drive", [(37, L.LBM_GEOM_BEAM, L.LBM_DRIVE_BODYFORCE),
+                                          (9, L.LBM_GEOM_PLATE, L.LBM_DRIVE_WALL),
+                                          (9, L.LBM_GEOM_BEAM, L.LBM_DRIVE_BODYFORCE)],
+                         ids=["q37-beam-body", "q9-plate-wall", "q9-beam-body"])
+def test_served_fp16_request_matches_oracle(Q, kind, drive):
+    """A served FP16 request (the mixed-precision form the server runs) against the FP64 oracle run
+    of the same solve from rest: the in-phase and quadrature force of the fit agree within the
+    stated 1e-4 of the force amplitude (error metric: |F_c - F_c^oracle| / sqrt(F_in^2 + F_q^2)).
+    The request is served among others (an FP32 D2Q37 one and an FP16 one of the other lattice)."""
+    import oracle as orc
+
+    nx, ny, lx, ly, u0 = 96, 64, 16, 12, 1e-3
+    P = 96
+    omega, tau = 2 * np.pi / P, 0.9
+    nsteps, skip = 3 * P, 1.0
+    eq = 4 if Q == 37 else 2
+    geo = dict(kind=kind, lx=lx, ly=ly, drive=drive, u0=u0, eq_order=eq, collision=L.LBM_COLL_REGULARIZED,
+               storage=L.LBM_STORE_F16)
+    perim = 2.0 * (lx + ly) if kind == L.LBM_GEOM_BEAM else float(nx)
+    target = L.make_request(L.make_instance(Q, nx, ny, tau, omega, nsteps, **geo), skip, perim)
+    other_q = 9 if Q == 37 else 37
+    others = [_req(37, 70, 41, 0.9, 0.05, 200),
+              _req(other_q, 80, 72, 0.8, 0.05, 250, storage=L.LBM_STORE_F16, lx=12, ly=9)]
+    out, _ = _serve([others[0], target, others[1]], [0.0, 0.0, 0.005])
+    res, hist = out[1]
+    lab = orc.geometry_beam(nx, ny, lx, ly) if kind == L.LBM_GEOM_BEAM else orc.geometry_plate(Q, nx, ny)
+    _, F_or = orc.run(Q, lab, tau, omega, u0, nsteps, eq_order=eq, collision=orc.COLL_REG, drive=drive,
+                      nthreads=orc.max_threads())
+    n0 = int(np.ceil(skip * 2 * np.pi / omega))   # the fit window of lbm_fit
+    f_in, f_q = orc.in_phase_quadrature(F_or[:, 0], omega, drive, skip=n0)
+    amp = float(np.hypot(f_in, f_q))
+    assert amp > 0
+    assert abs(res["f_in"] - f_in) <= 1e-4 * amp, (res["f_in"], f_in, amp)
+    assert abs(res["f_q"] - f_q) <= 1e-4 * amp, (res["f_q"], f_q, amp)
