@@ -7,7 +7,10 @@ Workloads (synthetic, shaped like the paper's cases):
   beam1024  D2Q37, 4th-order equilibrium, regularized collision, FP32 storage: a 32 x 32 beam
             section centred in a 1024^2 periodic box, body-frame drive, three instances at
             tau*omega = 0.01, 1, 10 (default).  One bench step advances every instance by one
-            lattice step (one fused kernel launch each).
+            lattice step (one fused kernel launch each).  The same run adds the rest of the metric
+            as extra keys: the 64-instance sweep in FP32 (one persistent launch) and in FP16 (both
+            batch modes), the 2048^2 precision study, and the served FP16 request stream (saturated,
+            at 70 % load, and its D2Q9 requests alone) with p50/p99 latency.
   plate9    D2Q9 plain BGK, FP64: the 4 x 256 oscillating plate (latency-bound correctness case).
   beam2048-<f32|f16|bf16|f64>  D2Q37-H4 beam in a 2048^2 box, tau*omega = 0.1, 1, 10.
   serve[-f16]  the serving loop: the first --requests requests of the seeded request stream (plate
@@ -19,8 +22,8 @@ Workloads (synthetic, shaped like the paper's cases):
   precision2048  precision study: the 2048^2 beam in FP64/FP32/FP16/BF16 storage, force errors
             against the FP64-storage run and MLUPS of each (prints its own JSON line).
   sweep64[-f16|-bf16]  the batched sweep: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides
-            256..1024) in one batch; a bench step is one batch step of all of them, and runs of
-            --chunk steps are single persistent cooperative launches.
+            256..1024) in one batch; a bench step is one batch step of all of them; with
+            --batch-mode 1, runs of --chunk steps are single launches of the persistent kernel.
 
 Each rank (torchrun, one per GPU) runs its own replicas: the instances are independent, so the
 work is sharded with no collective on the data path (weak scaling).  One JSON line is printed by
@@ -30,6 +33,7 @@ metric on a bounded sample (whole lattice, a few steps).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -46,16 +50,55 @@ sys.path.insert(0, ROOT)
 
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current step kernels,
-# from one ncu capture each (profiles/*.md); a kernel change invalidates its entry.
-TRAFFIC = {("beam1024", 1): 156.400384e6 + 108.256000e6,        # step_kernel_occ<D2Q37, float, 1, 6>
-           ("beam1024x1", 1): 156.400384e6 + 108.256000e6,
-           ("beam1024x1", 2): 156.415744e6 + 106.728448e6,      # step_kernel_occ<D2Q37, float, 1, 7>
-           ("beam1024x1-f16", 27): 78.824192e6 + 35.493120e6}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 11>
+# The metric of the default workload, printed by both arms (this library and the FP64 oracle).
+HEADLINE_METRIC = "MLUPS and % HBM roofline, batched mixed-prec vs plain FP32 at <=1e-4 force err; p99 latency"
+SUB_METRIC = "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction of the fused step"
+
+
+def metric_name(workload):
+    return HEADLINE_METRIC if workload == "beam1024" else SUB_METRIC
+
+
+def kernel_source_hash():
+    """Digest of the CUDA sources and the C ABI header: the DRAM traffic recorded below is valid
+    only for the sources it was captured from."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0904_4504_gb300", "csrc")
+    names = sorted(n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
+    for n in names:
+        h.update(n.encode())
+        with open(os.path.join(csrc, n), "rb") as fh:
+            h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "lbm.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the step kernels, from one
+# ncu capture each, with the digest of the sources they were captured from: once any source
+# changes, the entry no longer applies and the line reports traffic null.
+TRAFFIC = {}
+
+
+def traffic_for(workload, variant):
+    e = TRAFFIC.get((workload, variant))
+    if e is None or e[1] != kernel_source_hash():
+        return None
+    return e[0]
 # Thread instructions per fluid node (smsp__inst_executed.sum x 32 / fluid nodes) of the 16-bit step
-# kernel, from the same capture: with 16-bit storage the step is bound by instruction issue, so the
-# batched line also reports the issue rate against the SMs' issue peak.
-INST_PER_NODE = {("beam1024x1-f16", 27): 758.4}   # step_kernel_tman<D2Q37, half, 1, 64, 1, 3, 11>
+# kernel, from the same kind of capture and with the same digest rule: with 16-bit storage the step
+# is bound by instruction issue, so the batched line also reports the issue rate against the SMs'
+# issue peak.
+INST_PER_NODE = {}
+
+
+def inst_per_node(workload, variant):
+    e = INST_PER_NODE.get((workload, variant))
+    if e is None or e[1] != kernel_source_hash():
+        return None
+    return e[0]
+
+
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 
@@ -187,7 +230,7 @@ def issue_roofline(bl):
     SMs' issue peak (4 schedulers per SM, one warp instruction per scheduler per cycle, at the
     median SM clock sampled during the run); None without a captured instruction count."""
     import torch
-    ipn = INST_PER_NODE.get(("beam1024x1-f16", bl["config"].get("kernel_variant")))
+    ipn = inst_per_node("beam1024x1-f16", bl["config"].get("kernel_variant"))
     mhz = (bl.get("clocks") or {}).get("sm_mhz")
     if not ipn or not mhz:
         return None
@@ -283,7 +326,7 @@ def run_batch(args, sub=False):
                         "64 lbm_force_history"}
     if rank == 0:
         line = {
-            "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction of the fused step",
+            "metric": metric_name(args.workload),
             "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {v: k for k, v in STORE.items()}[storage], "data": "synthetic",
@@ -292,11 +335,13 @@ def run_batch(args, sub=False):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
                        "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout,
-                       "kernel_variant": used[0] if len(used) == 1 else used},
+                       "kernel_variant": used[0] if len(used) == 1 else used,
+                       "segment_tiles": args.batch_segment or "library default"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "batch_kernel (persistent, cooperative)" if info["mode"] == 1 else
+                         "kernel": "pbatch_kernel (persistent; per-row step counters, no grid barrier; one CUDA "
+                                   "graph launch per run)" if info["mode"] == 1 else
                                    "step kernels of every instance on parallel streams",
                          "bytes_per_batch_step": bytes_step},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": None,
@@ -403,7 +448,7 @@ def run_serve(args, sub=False):
         dist.destroy_process_group()
 
 
-def run_precision(args):
+def run_precision(args, sub=False):
     """Precision study at full size: the D2Q37-H4 beam in 2048^2 at tau*omega = 0.1, 1, 10 for 30
     periods in every storage type; in-phase/quadrature force error of each against the FP64-storage
     run (the FP64 oracle comparison on the 256^2 downscale is tests/test_gpu_precision.py)."""
@@ -411,8 +456,9 @@ def run_precision(args):
     from paper_0904_4504_gb300 import inputs as I
     from paper_0904_4504_gb300 import lbm as L
     from paper_0904_4504_gb300.builder import build
+    from paper_0904_4504_gb300.replicas import env_rank
 
-    rank, world, local = dist_setup(args.gpus)
+    rank, world, local = env_rank() if sub else dist_setup(args.gpus)
     build()
     stream = torch.cuda.Stream()
     out = []
@@ -444,10 +490,16 @@ def run_precision(args):
         for name in fits:
             row[f"mlups_{name}"] = round(fits[name][2], 1)
         out.append(row)
+    line = {"study": "precision", "workload": "D2Q37-H4 regularized beam 32x32 in 2048^2, body-frame drive U0=1e-3, "
+            "30 periods, fit after 15; force errors (in-phase, quadrature) of FP32/FP16/BF16 storage against the "
+            "FP64-storage run, normalized by the FP64 force amplitude; FP32 arithmetic, FP64 force sums",
+            "rows": out,
+            "max_err": {name: max(max(r[f"err_in_{name}"], r[f"err_q_{name}"]) for r in out)
+                        for name in ("f32", "f16", "bf16")}}
+    if sub:
+        return line
     if rank == 0:
-        print(json.dumps({"study": "precision", "workload": "D2Q37-H4 regularized beam 32x32 in 2048^2, body-frame "
-                          "drive U0=1e-3, 30 periods, fit after 15; errors normalized by the FP64 force amplitude",
-                          "rows": out}), flush=True)
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
@@ -530,41 +582,63 @@ def run_ours(args):
     cpu = cpu_baseline(wl, params, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
     extras = {}
     if args.workload == "beam1024" and not args.no_extras:
-        # the rest of the metric: the batched mixed-precision form (FP16 storage, FP32 arithmetic,
-        # FP64 force; within the 1e-4 force target) against this plain FP32 single-instance form,
-        # and the served p50/p99 latency
+        # the rest of the metric: the batched forms (FP32 as one persistent launch; mixed precision
+        # -- FP16 storage, FP32 arithmetic, FP64 force -- in both batch modes) against this plain
+        # FP32 single-instance form, the precision study at 2048^2, and the served mixed-precision
+        # stream with its p50/p99 latency
         import copy
-        a = copy.copy(args)
-        a.workload, a.steps, a.warmup, a.no_e2e = "sweep64-f16", args.sweep_steps, 3, True
-        bl = run_batch(a, sub=True)
-        a = copy.copy(args)
-        a.workload, a.requests, a.load = "serve", args.requests, args.load
-        sl = run_serve(a, sub=True)
-        # the served mixed-precision form at saturation: the request stream as generated offers
-        # 10-25x the GPU's capacity, so the server always has work; a 6 GB device budget keeps a
-        # few dozen lattices resident, and 96 requests make the admit-as-others-finish steady state
-        # most of the run
-        a = copy.copy(args)
-        a.workload, a.requests, a.load, a.serve_budget_gb = "serve-f16", 96, 0.0, 6.0
-        sm = run_serve(a, sub=True)
+
+        def batch_line(workload, mode, chunk, steps):
+            a = copy.copy(args)
+            a.workload, a.steps, a.warmup, a.no_e2e, a.batch_mode, a.chunk = workload, steps, 3, True, mode, chunk
+            a.batch_variant, a.batch_segment, a.instances = None, 0, 0
+            return run_batch(a, sub=True)
+
+        def serve_line(requests, load, lattice):
+            a = copy.copy(args)
+            a.workload, a.requests, a.load, a.serve_budget_gb, a.serve_lattice = "serve-f16", requests, load, 6.0, lattice
+            return run_serve(a, sub=True)
+
+        b32 = batch_line("sweep64", 1, args.sweep_steps, args.sweep_steps)
+        b16 = batch_line("sweep64-f16", 0, 64, args.sweep_steps)
+        p16 = batch_line("sweep64-f16", 1, 64, args.sweep_steps)
+        prec = run_precision(args, sub=True) if not args.no_precision else None
+        sm = serve_line(args.requests, 0.0, 0)
+        s70 = serve_line(max(1, args.requests // 2), 0.7, 0)
+        s9 = serve_line(max(1, args.requests // 2), 0.0, 9)
         if rank == 0:
-            extras["batched_mixed_precision"] = {
-                "workload": "sweep64-f16: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024), "
-                            "streams mode (one launch of the staged step kernel per instance per step, on 16 "
-                            "parallel streams), FP16 storage scaled by U0, FP32 arithmetic, FP64 force",
-                "value": bl["value"], "unit": "MLUPS", "steps": bl["steps"], "ms_per_step": bl["ms_per_step"],
-                "roofline": bl["roofline"], "clocks": bl["clocks"], "gpu_launches": bl["gpu_launches"],
-                "speedup_vs_plain_fp32": round(bl["value"] / value, 4),
-                "issue": issue_roofline(bl),
-                "force_error_vs_oracle": "FP16 storage <= 1.6e-5 of the force amplitude (in-phase and quadrature, "
-                                         "body and lab frame, tests/test_gpu_precision.py); target 1e-4"}
-            extras["serving"] = {k: sl[k] for k in ("value", "unit", "config", "latency", "server", "clocks")}
-            extras["serving_mixed_precision_saturated"] = {
-                k: sm[k] for k in ("value", "unit", "config", "roofline", "latency", "server", "clocks")}
+            def keep(line, *keys):
+                return {k: line[k] for k in keys if k in line}
+            extras["batched_fp32_persistent"] = dict(
+                keep(b32, "value", "unit", "steps", "ms_per_step", "roofline", "clocks", "gpu_launches", "config"),
+                workload="sweep64: 64 D2Q37-H4 beam instances (16 tau*omega x 4 AR, sides 256..1024), FP32, all "
+                         "timed steps in one launch of the persistent kernel through a CUDA graph",
+                speedup_vs_plain_fp32=round(b32["value"] / value, 4))
+            extras["batched_mixed_precision"] = dict(
+                keep(b16, "value", "unit", "steps", "ms_per_step", "roofline", "clocks", "gpu_launches", "config"),
+                workload="sweep64-f16: the same 64 instances, streams mode (one launch of the staged step kernel "
+                         "per instance per step, on 16 parallel streams), FP16 storage scaled by U0, FP32 "
+                         "arithmetic, FP64 force",
+                speedup_vs_plain_fp32=round(b16["value"] / value, 4), issue=issue_roofline(b16),
+                force_error_vs_oracle="FP16 storage <= 1.6e-5 of the force amplitude (in-phase and quadrature, body "
+                                      "and lab frame, tests/test_gpu_precision.py); target 1e-4")
+            extras["batched_mixed_precision_persistent"] = dict(
+                keep(p16, "value", "unit", "steps", "ms_per_step", "roofline", "clocks", "gpu_launches", "config"),
+                workload="sweep64-f16 in the persistent mode: one launch per 64 steps of the persistent kernel "
+                         "(staged 64 x 3 tiles) through a CUDA graph",
+                speedup_vs_plain_fp32=round(p16["value"] / value, 4))
+            if prec is not None:
+                extras["precision_study"] = prec
+            extras["serving_mixed_precision_saturated"] = keep(sm, "value", "unit", "config", "roofline", "latency",
+                                                               "server", "clocks")
+            extras["serving_mixed_precision_70pct"] = keep(s70, "value", "unit", "config", "roofline", "latency",
+                                                           "server", "clocks")
+            extras["serving_d2q9_saturated"] = keep(s9, "value", "unit", "config", "roofline", "latency", "server",
+                                                    "clocks")
     if rank == 0:
         w0 = wl[0]
         line = {
-            "metric": "MLUPS and % HBM roofline, batched mixed-prec vs plain FP32 at <=1e-4 force err; p99 latency",
+            "metric": metric_name(args.workload),
             "value": round(value, 3), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_max / args.steps, 6), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE_NAME[w0.storage], "data": "synthetic",
@@ -578,7 +652,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": args.traffic if args.traffic is not None else
-                         TRAFFIC.get((args.workload, infos[0]["variant"])) if args.layout == "ab" else None,
+                         traffic_for(args.workload, infos[0]["variant"]) if args.layout == "ab" else None,
                          "peak_source": f"{peak_kind} hbm_gbs", "kernel": "fused stream+collide+force step (kernel variant in config)",
                          "bytes_per_launch": bytes_step // len(wl)},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
@@ -651,8 +725,7 @@ def run_reference(args):
     v = done / dt / 1e6
     w0 = wl[0]
     print(json.dumps({
-        "impl": "reference", "metric": "MLUPS (fluid lattice updates per second, whole job) and HBM-roofline fraction "
-                                       "of the fused step",
+        "impl": "reference", "metric": metric_name(args.workload),
         "value": round(v, 4), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -676,7 +749,9 @@ def main():
     ap.add_argument("--layout", default="ab", choices=["ab", "aa"],
                     help="population layout: two buffers (ab) or one buffer updated in place (aa)")
     ap.add_argument("--chunk", type=int, default=64, help="batch steps per persistent launch (sweep64, serve)")
-    ap.add_argument("--requests", type=int, default=24, help="requests per rank (serve)")
+    ap.add_argument("--requests", type=int, default=400,
+                    help="requests per rank (serve; the default workload's saturated serving line; its 70%%-load and "
+                         "D2Q9 lines take half as many)")
     ap.add_argument("--serve-lattice", type=int, default=0, choices=[0, 9, 37],
                     help="serve: only the requests of this lattice (0: all)")
     ap.add_argument("--serve-budget-gb", type=float, default=0.0,
@@ -684,6 +759,7 @@ def main():
     ap.add_argument("--load", type=float, default=0.7, help="offered load, fraction of capacity (serve; 0: as generated)")
     ap.add_argument("--sweep-steps", type=int, default=640, help="timed batch steps of the batched part of beam1024")
     ap.add_argument("--no-extras", action="store_true", help="beam1024: skip the batched and serving parts")
+    ap.add_argument("--no-precision", action="store_true", help="beam1024: skip the 2048^2 precision study")
     ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
     ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
     ap.add_argument("--batch-variant", type=int, default=None, help="sweep64: step kernel of the streams mode")

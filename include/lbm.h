@@ -398,6 +398,10 @@ int lbm_server_create(size_t device_budget_bytes, int steps_per_round, lbm_serve
 /* Queue a request (returns at once).  LBM_ENOMEM if it could never fit the budget. */
 int lbm_server_submit(lbm_server* server, const lbm_request* req, long long* id);
 
+/* Mode of the class batches the server creates from now on (lbm_batch_set_mode; default
+ * LBM_BATCH_STREAMS).  Call it before the first lbm_server_submit so that every class uses it. */
+int lbm_server_set_batch_mode(lbm_server* server, int mode);
+
 /* Copy a request's result; returns 1 when it has finished (done or failed), 0 otherwise. */
 int lbm_server_poll(lbm_server* server, long long id, lbm_result* out);
 

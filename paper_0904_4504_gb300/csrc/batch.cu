@@ -364,9 +364,10 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     } else {
         // default kernels, fastest measured in this mode: for D2Q37, the staged kernel with three
         // rows per thread (27) for 16-bit storage and the plain kernel with 7 resident blocks per SM
-        // (2) for FP32; 16-bit D2Q9 takes the staged kernel 10; else the plain kernel
+        // (2) for FP32; 16-bit D2Q9 takes the four-nodes-per-thread kernel (30); else the plain
+        // kernel
         const int want = b->variant >= 0 ? b->variant
-                         : half ? (b->Q == 37 ? 27 : 10)
+                         : half ? (b->Q == 37 ? 27 : 30)
                          : (b->Q == 37 && b->storage == LBM_STORE_F32) ? 2 : 0;
         if (want == 0 || lbm_set_variant(sim, want) != LBM_OK) rc = lbm_set_tile(sim, b->bx, b->by);
     }

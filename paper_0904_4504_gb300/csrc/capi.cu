@@ -24,6 +24,7 @@
 namespace lbm {
 
 void* find_tma_launcher_q9(int storage, int coll, int variant);
+void* find_q9v_launcher(int storage, int coll);
 void tma_box_q9(int storage, int bx, int* bw, int* pad);
 
 // D2Q37 launch tables, one translation unit per storage type (step_q37_inst.cuh).
@@ -83,6 +84,7 @@ static bool variant_tile(int variant, int* bx, int* by) {
         case 26:
         case 27: *bx = 64; *by = 3; return true;
         case 20: *bx = 64; *by = 4; return true;
+        case 30: *bx = 128; *by = 4; return true;
         case 21: *bx = 64; *by = 2; return true;
         case 22: *bx = 128; *by = 2; return true;
         default: return false;
@@ -869,14 +871,24 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     d.src_k_f = (float)d.src_k;
     s->stream_off = es == 2 && g.drive == LBM_DRIVE_BODYFORCE;
     d.stream_off = s->stream_off ? 1 : 0;
-    // default kernel on the default 32 x 4 tile: the fastest measured single-instance form, the
-    // plain kernel with an occupancy floor (variant 1 for FP32, 2 for 16-bit storage)
+    // default kernel: the fastest measured single-instance form -- for D2Q37 the plain kernel with
+    // an occupancy floor on the default 32 x 4 tile (variant 1 for FP32, 2 for 16-bit storage), for
+    // 16-bit D2Q9 the four-nodes-per-thread kernel on 128 x 4 tiles (variant 30)
     if (!s->aa && g.wall_scheme == LBM_SCHEME_BOUNCEBACK) {
-        const int v = es == 4 ? 1 : es == 2 ? 2 : 0;
-        StepLaunchFn f = v ? find_occ_launcher(lattice, g.storage, g.collision, v) : nullptr;
-        if (f) {
-            s->launch = f;
-            s->variant = v;
+        if (lattice == LBM_D2Q9 && es == 2) {
+            StepLaunchFn f = reinterpret_cast<StepLaunchFn>(find_q9v_launcher(g.storage, g.collision));
+            if (f) {
+                s->launch = f;
+                s->variant = 30;
+                variant_tile(30, &s->bx, &s->by);
+            }
+        } else {
+            const int v = es == 4 ? 1 : es == 2 ? 2 : 0;
+            StepLaunchFn f = v ? find_occ_launcher(lattice, g.storage, g.collision, v) : nullptr;
+            if (f) {
+                s->launch = f;
+                s->variant = v;
+            }
         }
     }
     TRY_OR_FREE(setup_tiles(s));
@@ -907,8 +919,11 @@ int lbm_set_variant(lbm_sim* s, int variant) {
     if (s->aa) return set_error(LBM_EINVAL, "the in-place (AA) layout runs the plain kernel (variant 0) only");
     if (s->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
         return set_error(LBM_EINVAL, "kernel variants are built for bounce-back walls only");
-    if (variant >= 1 && variant <= 4) {
-        StepLaunchFn f = find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
+    if ((variant >= 1 && variant <= 4) || variant == 30) {
+        StepLaunchFn f = variant == 30 ? (s->Q == 9 ? reinterpret_cast<StepLaunchFn>(
+                                                          find_q9v_launcher(s->geom.storage, s->geom.collision))
+                                                    : nullptr)
+                                       : find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
         if (!f) return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);
         CUDA_TRY(cudaStreamSynchronize(s->stream));
         variant_tile(variant, &s->bx, &s->by);

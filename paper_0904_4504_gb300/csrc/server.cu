@@ -1,11 +1,13 @@
 // server.cu -- continuous-batching request loop (lbm_server_* in include/lbm.h).
 //
 // A worker thread owns one batch per (lattice, storage, collision) class, all on one stream.
-// Each round it enqueues a persistent run of K steps for every class with running instances, then
-// -- while the GPU works -- admits waiting requests in arrival order as long as their device
+// Each round it enqueues a run of K steps (lbm_batch_run) for every class with running instances,
+// then -- while the GPU works -- admits waiting requests in arrival order as long as their device
 // footprint fits the budget (they join the next round), waits for the round, and retires the
 // instances that have run all their steps: FP64 fit of the force history, normalized damping,
-// memory freed.  Clients submit and poll from any thread.
+// memory freed.  The batches run in their default mode, the streams mode (every instance's step
+// kernel on one of 16 parallel streams; the persistent mode is lbm_server_set_batch_mode).
+// Clients submit and poll from any thread.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +47,7 @@ struct lbm_server {
     int device = 0;
     size_t budget = 0, used = 0;
     int steps_per_round = 64;
+    int batch_mode = LBM_BATCH_STREAMS;  // mode of the class batches created from now on
     cudaStream_t stream = nullptr;
     std::map<int, lbm_batch*> batches;
     // shared with clients
@@ -95,6 +98,12 @@ void admit(lbm_server* s) {
         if (!b) {
             rc = lbm_batch_create(j->req.desc.lattice, j->req.desc.geom.storage, j->req.desc.geom.collision, s->budget,
                                   &b);
+            int mode = LBM_BATCH_STREAMS;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                mode = s->batch_mode;
+            }
+            if (rc == LBM_OK && mode != LBM_BATCH_STREAMS) rc = lbm_batch_set_mode(b, mode);
             if (rc == LBM_OK) rc = lbm_batch_set_stream(b, s->stream);
         }
         if (rc == LBM_OK) rc = lbm_batch_add(b, &j->req.desc, &j->slot);
@@ -270,6 +279,14 @@ int lbm_server_submit(lbm_server* s, const lbm_request* req, long long* id) {
     s->incoming.push_back(j);
     s->cv_work.notify_one();
     *id = j->id;
+    return LBM_OK;
+}
+
+int lbm_server_set_batch_mode(lbm_server* s, int mode) {
+    if (!s) return set_error(LBM_EINVAL, "null server");
+    if (mode != LBM_BATCH_STREAMS && mode != LBM_BATCH_PERSISTENT) return set_error(LBM_EINVAL, "bad batch mode");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->batch_mode = mode;
     return LBM_OK;
 }
 

@@ -1,5 +1,6 @@
 // D2Q9 instantiations of the fused step (all storage types, both collisions).
 #include "pbatch.cuh"
+#include "step_q9v.cuh"
 
 namespace lbm {
 
@@ -50,6 +51,19 @@ PbKernel find_pbatch_q9(int storage, int coll, int path) {
         case ST_BF16: return q9_pbatch_s<__nv_bfloat16>(coll, path);
         case ST_F16: return q9_pbatch_s<__half>(coll, path);
         default: return PbKernel{nullptr, dim3(), 0, 0, 0};
+    }
+}
+
+// The four-nodes-per-thread kernel of 16-bit storage (variant 30, tiles of 128 x 4; step_q9v.cuh).
+void* find_q9v_launcher(int storage, int coll) {
+    switch (storage * 2 + coll) {
+        // the regularized collision fits 80 registers (6 blocks per SM); plain BGK keeps the nine
+        // pulled values live for its outputs and takes 5
+        case ST_BF16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_BGK, 5>;
+        case ST_BF16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_REG, 6>;
+        case ST_F16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__half, COLL_BGK, 5>;
+        case ST_F16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__half, COLL_REG, 6>;
+        default: return nullptr;
     }
 }
 

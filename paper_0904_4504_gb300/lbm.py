@@ -205,6 +205,7 @@ def lib():
             "lbm_batch_destroy": (None, [_P]),
             "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
             "lbm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_longlong)]),
+            "lbm_server_set_batch_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(lbm_result)]),
             "lbm_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(lbm_result)]),
             "lbm_server_force_history": (ctypes.c_int, [_P, ctypes.c_longlong, _D, ctypes.c_size_t,
@@ -486,6 +487,10 @@ def make_request(desc: lbm_instance_desc, skip_periods: float, perimeter: float 
     r = lbm_request(desc, skip_periods, perimeter)
     r._desc_ref = desc
     return r
+
+
+def lbm_server_set_batch_mode(server: int, mode: int) -> None:
+    _check(lib().lbm_server_set_batch_mode(server, mode))
 
 
 def lbm_server_submit(server: int, req: lbm_request) -> int:

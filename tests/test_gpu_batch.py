@@ -44,7 +44,7 @@ def batch_kernel_variant(d, mode=L.LBM_BATCH_STREAMS):
             return 27
         return 2 if (d.lattice == 37 and g.storage != L.LBM_STORE_F64) else 0
     if half:
-        return 27 if d.lattice == 37 else 10
+        return 27 if d.lattice == 37 else 30
     return 2 if (d.lattice == 37 and g.storage == L.LBM_STORE_F32) else 0
 
 

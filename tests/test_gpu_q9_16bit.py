@@ -2,9 +2,11 @@
 
 The served mixed-precision stream runs D2Q9 instances in FP16 (plates and beams), so every D2Q9
 kernel built for 16-bit storage is checked here: the plain kernel (variant 0), the staged kernel
-(variant 10, TMA boxes on 32 x 4 tiles) and the paired kernel (variant 20, two neighbouring nodes
-per thread on 64 x 4 tiles).  Grids are 200 x 90 / 203 x 61: interior (staged) tiles, tiles on the
-periodic edges (plain loads) and a ragged last tile.
+(variant 10, TMA boxes on 32 x 4 tiles), the paired kernel (variant 20, two neighbouring nodes
+per thread on 64 x 4 tiles) and the vector kernel (variant 30, four neighbouring nodes per thread
+with 8-byte loads and stores on 128 x 4 tiles).  Grids are 200 x 90 / 203 x 61: interior (staged)
+tiles, tiles on the periodic edges (plain loads), warps whose lanes meet the periodic seam, and a
+ragged last tile (203 = 4 x 50 + 3: the per-node path of the vector kernel).
 
 Bound (see test_gpu_parity.py): one step from a 16-bit-exact state must give the exact step
 rounded once to the storage type, i.e. within 2^-8 (BF16) or 2^-11 (FP16) of each value (relative
@@ -30,7 +32,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 ST16 = [L.LBM_STORE_BF16, L.LBM_STORE_F16]
-VARIANTS = [0, 10, 20]
+VARIANTS = [0, 10, 20, 30]
 # (geometry, drive): the beam in the body frame (stream offset on) and the plate with its moving
 # wall (the D2Q9 plate workload), and a lab-frame beam
 GEOMS = [(L.LBM_GEOM_BEAM, L.LBM_DRIVE_BODYFORCE), (L.LBM_GEOM_PLATE, L.LBM_DRIVE_WALL),

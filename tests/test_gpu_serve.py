@@ -38,9 +38,10 @@ REQS = [
 ]
 
 
-def _serve(reqs, delays, budget=0, k=16):
+def _serve(reqs, delays, budget=0, k=16, mode=L.LBM_BATCH_STREAMS):
     srv = L.lbm_server_create(budget, k)
     try:
+        L.lbm_server_set_batch_mode(srv, mode)
         ids = []
         for r, dly in zip(reqs, delays):
             time.sleep(dly)
@@ -56,12 +57,13 @@ def _serve(reqs, delays, budget=0, k=16):
     return out, stats
 
 
-def test_served_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("mode", [L.LBM_BATCH_STREAMS, L.LBM_BATCH_PERSISTENT], ids=["streams", "persistent"])
+def test_served_result_is_the_same_alone_and_in_the_mix(mode):
     reqs = [_req(Q, nx, ny, tau, om, n, **kw) for Q, nx, ny, tau, om, n, kw in REQS]
-    mixed, stats = _serve(reqs, [0.0, 0.0, 0.01, 0.0, 0.02, 0.0])
+    mixed, stats = _serve(reqs, [0.0, 0.0, 0.01, 0.0, 0.02, 0.0], mode=mode)
     assert stats["completed"] == len(reqs) and stats["peak_running"] >= 2
     for r, (res_m, hist_m) in zip(reqs, mixed):
-        (res_a, hist_a), = _serve([r], [0.0])[0]
+        (res_a, hist_a), = _serve([r], [0.0], mode=mode)[0]
         assert hist_m.shape == hist_a.shape == (r.desc.nsteps, 2)
         assert (hist_m == hist_a).all()
         for key in ("f_in", "f_q", "f_0", "gamma_bar"):
