@@ -102,6 +102,12 @@ def inst_per_node(workload, variant):
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16", 3: "f16"}
 
 
+def tune_cache_path():
+    """JSON cache of the batch autotuner for this machine's runs (a fresh box tunes once)."""
+    import tempfile
+    return os.path.join(tempfile.gettempdir(), "lbm_gb300_bench_tune.json")
+
+
 def workload_list(name):
     from paper_0904_4504_gb300 import inputs as I
     if name == "beam1024":
@@ -261,6 +267,12 @@ def run_batch(args, sub=False):
         L.lbm_batch_set_variant(b, args.batch_variant)
     if args.batch_segment:
         L.lbm_batch_set_segment(b, args.batch_segment)
+    tuned = None
+    if args.batch_autotune:
+        from paper_0904_4504_gb300 import autotune as A
+        t0 = time.perf_counter()
+        tuned = A.tune_batch(b, [d for _, d in descs], tune_cache_path(), steps=8)
+        tuned = dict(tuned, tune_s=round(time.perf_counter() - t0, 2))
     L.lbm_batch_set_stream(b, stream)
     slots = [L.lbm_batch_add(b, d) for _, d in descs]
     info0 = L.lbm_batch_info(b)
@@ -310,6 +322,9 @@ def run_batch(args, sub=False):
             L.lbm_batch_set_variant(b, args.batch_variant)
         if args.batch_segment:
             L.lbm_batch_set_segment(b, args.batch_segment)
+        if args.batch_autotune:
+            from paper_0904_4504_gb300 import autotune as A
+            A.tune_batch(b, [d for _, d in descs], tune_cache_path(), steps=8)   # the cached choice
         slots = [L.lbm_batch_add(b, d) for _, d in descs]
         run(args.steps)
         L.lbm_batch_synchronize(b)
@@ -336,7 +351,8 @@ def run_batch(args, sub=False):
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
                        "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout,
                        "kernel_variant": used[0] if len(used) == 1 else used,
-                       "segment_tiles": args.batch_segment or "library default"},
+                       "segment_tiles": args.batch_segment or "library default",
+                       "autotuned": tuned},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
@@ -388,6 +404,15 @@ def run_serve(args, sub=False):
     else:
         arrivals = np.array([a for a, _ in reqs]) - reqs[0][0]
     srv = L.lbm_server_create(int(args.serve_budget_gb * 1e9), args.chunk)
+    tuned = None
+    if args.batch_autotune:
+        # each request class's kernel, chosen by the batch autotuner on a sample of the class's
+        # requests before the first submit (outside the timed region)
+        from paper_0904_4504_gb300 import autotune as A
+        t0 = time.perf_counter()
+        ch = A.tune_server(srv, [rq for _, rq in reqs], tune_cache_path(), steps=4, sample=8)
+        tuned = {f"Q{k[0]}-st{k[1]}-coll{k[2]}": v for k, v in ch.items()}
+        tuned["tune_s"] = round(time.perf_counter() - t0, 2)
     ids = []
     torch.cuda.synchronize()
     barrier(world)
@@ -426,7 +451,8 @@ def run_serve(args, sub=False):
             "config": {"workload": args.workload, "requests": len(reqs), "offered_load": args.load or "as generated",
                        "lattices": args.serve_lattice or "D2Q9 and D2Q37",
                        "budget_gb": args.serve_budget_gb or "server default",
-                       "steps_per_round": args.chunk, "parallelism": f"replicas x{world}", "layout": args.layout},
+                       "steps_per_round": args.chunk, "parallelism": f"replicas x{world}", "layout": args.layout,
+                       "autotuned": tuned},
             "latency": {"p50_s": round(float(np.percentile(lat, 50)), 4),
                         "p99_s": round(float(np.percentile(lat, 99)), 4), "mean_s": round(float(lat.mean()), 4),
                         "max_s": round(float(lat.max()), 4)},
@@ -763,6 +789,9 @@ def main():
     ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
     ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
     ap.add_argument("--batch-variant", type=int, default=None, help="sweep64: step kernel of the streams mode")
+    ap.add_argument("--batch-autotune", type=int, default=1,
+                    help="sweep64/serve: choose the batch kernels with the batch autotuner (JSON cache in the temp "
+                         "dir) before the timed region (1) or use the library's defaults (0)")
     ap.add_argument("--batch-segment", type=int, default=0,
                     help="sweep64, persistent mode: tiles per work item (0: the library's default)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")

@@ -346,6 +346,28 @@ int lbm_batch_set_barrier_limit(lbm_batch* batch, long long cycles);
 
 int lbm_batch_info(lbm_batch* batch, lbm_batch_info_t* out);
 
+/* Batch autotuning: the kernel a batch runs is chosen by timing the candidates on the instances
+ * themselves, under batch conditions (concurrent streams or the persistent kernel over all of them),
+ * since a kernel's speed alone and in a batch differ.  Each candidate runs a temporary batch of
+ * clones of `descs` (as many as the batch's budget holds) in this batch's mode for 2 + steps batch
+ * steps, the last `steps` timed.  Candidates: in the streams mode the step-kernel variants built for
+ * the class (variant; segment 0); in the persistent mode its two tile paths (variant 27 staged,
+ * 2 plain) times segment lengths 1, 2, 4, 8.  Needs device memory for the clones. */
+typedef struct {
+    int variant;               /* lbm_batch_set_variant number                                   */
+    int segment;               /* persistent mode: tiles per work item (lbm_batch_set_segment)   */
+    double us_per_step;        /* time of one batch step of the clones                           */
+} lbm_batch_tune_entry;
+
+/* Time the candidates; fills up to cap entries of out, *n receives the number timed. */
+int lbm_batch_tune(lbm_batch* batch, const lbm_instance_desc* descs, int n, int steps, lbm_batch_tune_entry* out,
+                   int cap, int* n_out);
+
+/* lbm_batch_tune, then set the fastest candidate on the batch (which must hold no instance yet);
+ * *best receives it if not NULL. */
+int lbm_batch_autotune(lbm_batch* batch, const lbm_instance_desc* descs, int n, int steps,
+                       lbm_batch_tune_entry* best);
+
 /* Run the batch on `stream` (caller-owned cudaStream_t; 0 is the default stream). */
 int lbm_batch_set_stream(lbm_batch* batch, void* stream);
 
@@ -401,6 +423,12 @@ int lbm_server_submit(lbm_server* server, const lbm_request* req, long long* id)
 /* Mode of the class batches the server creates from now on (lbm_batch_set_mode; default
  * LBM_BATCH_STREAMS).  Call it before the first lbm_server_submit so that every class uses it. */
 int lbm_server_set_batch_mode(lbm_server* server, int mode);
+
+/* Kernel of one (lattice, storage, collision) class of requests: the class batch the server creates
+ * from now on gets lbm_batch_set_variant(variant) and, in the persistent mode,
+ * lbm_batch_set_segment(segment) (0: the default) -- e.g. the choice lbm_batch_tune made on a sample
+ * of the class's requests.  LBM_EINVAL for a variant below -1 or a negative segment. */
+int lbm_server_set_class_kernel(lbm_server* server, int lattice, int storage, int collision, int variant, int segment);
 
 /* Copy a request's result; returns 1 when it has finished (done or failed), 0 otherwise. */
 int lbm_server_poll(lbm_server* server, long long id, lbm_result* out);

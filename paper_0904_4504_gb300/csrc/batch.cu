@@ -604,6 +604,94 @@ int lbm_batch_set_variant(lbm_batch* b, int variant) {
     return LBM_OK;
 }
 
+int lbm_batch_tune(lbm_batch* b, const lbm_instance_desc* descs, int n, int steps, lbm_batch_tune_entry* out, int cap,
+                   int* n_out) {
+    int rc = check_batch(b);
+    if (rc) return rc;
+    if (!descs || n < 1 || steps < 1 || !n_out || (cap > 0 && !out))
+        return set_error(LBM_EINVAL, "need instance descriptions, steps >= 1 and an output");
+    // candidates: streams mode, the step kernels of the class; persistent mode, its tile paths
+    // (staged 27, plain 2) times the segment lengths
+    std::vector<lbm_batch_tune_entry> cand;
+    if (b->mode == LBM_BATCH_STREAMS) {
+        for (int v : {0, 1, 2, 10, 20, 26, 27, 30}) cand.push_back(lbm_batch_tune_entry{v, 0, 0.0});
+    } else {
+        for (int v : {27, 2})
+            if (find_pbatch_kernel(b->Q, b->storage, b->collision, v == 27 ? PB_STAGED : PB_PLAIN).func)
+                for (int sg : {1, 2, 4, 8}) cand.push_back(lbm_batch_tune_entry{v, sg, 0.0});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return set_error(LBM_ECUDA, "event creation");
+    }
+    int k = 0;
+    const int warm = 2;
+    for (auto& e : cand) {
+        lbm_batch* t = nullptr;
+        if ((rc = lbm_batch_create(b->Q, b->storage, b->collision, b->budget, &t))) break;
+        rc = lbm_batch_set_mode(t, b->mode);
+        if (rc == LBM_OK) rc = lbm_batch_set_variant(t, e.variant);
+        if (rc == LBM_OK && b->mode == LBM_BATCH_PERSISTENT) rc = lbm_batch_set_segment(t, e.segment);
+        bool usable = rc == LBM_OK;
+        int added = 0;
+        for (int j = 0; usable && j < n; ++j) {
+            lbm_instance_desc d = descs[j];
+            d.nsteps = warm + steps;
+            int slot = -1;
+            const int r = lbm_batch_add(t, &d, &slot);
+            if (r == LBM_ENOMEM) break;  // the clones fill the budget: time the ones that fit
+            if (r != LBM_OK) { rc = r; usable = false; break; }
+            // a streams-mode variant that the class does not build falls back to the plain kernel:
+            // not a distinct candidate
+            if (b->mode == LBM_BATCH_STREAMS && sim_view(t->slots[slot].sim).variant != e.variant) usable = false;
+            ++added;
+        }
+        clear_error();
+        if (usable && added > 0) {
+            rc = lbm_batch_run(t, warm);
+            if (rc == LBM_OK && cudaEventRecord(e0, t->stream) != cudaSuccess) rc = set_error(LBM_ECUDA, "event");
+            if (rc == LBM_OK) rc = lbm_batch_run(t, steps);
+            if (rc == LBM_OK && cudaEventRecord(e1, t->stream) != cudaSuccess) rc = set_error(LBM_ECUDA, "event");
+            if (rc == LBM_OK) rc = lbm_batch_synchronize(t);
+            if (rc == LBM_OK) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                e.us_per_step = 1000.0 * ms / steps;
+                if (k < cap) out[k] = e;
+                ++k;
+            }
+        } else if (rc == LBM_EINVAL) {
+            rc = LBM_OK;  // candidate not built for this class
+            clear_error();
+        }
+        lbm_batch_destroy(t);
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *n_out = k;
+    return rc;
+}
+
+int lbm_batch_autotune(lbm_batch* b, const lbm_instance_desc* descs, int n, int steps, lbm_batch_tune_entry* best) {
+    int rc = check_batch(b);
+    if (rc) return rc;
+    for (const Slot& s : b->slots)
+        if (slot_live(s)) return set_error(LBM_EINVAL, "tune the batch before adding instances");
+    lbm_batch_tune_entry e[32];
+    int m = 0;
+    if ((rc = lbm_batch_tune(b, descs, n, steps, e, 32, &m))) return rc;
+    if (m == 0) return set_error(LBM_EINVAL, "no candidate could be timed");
+    int k = 0;
+    for (int j = 1; j < m; ++j)
+        if (e[j].us_per_step < e[k].us_per_step) k = j;
+    if ((rc = lbm_batch_set_variant(b, e[k].variant))) return rc;
+    if (b->mode == LBM_BATCH_PERSISTENT && (rc = lbm_batch_set_segment(b, e[k].segment))) return rc;
+    if (best) *best = e[k];
+    return LBM_OK;
+}
+
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);

@@ -48,6 +48,7 @@ struct lbm_server {
     size_t budget = 0, used = 0;
     int steps_per_round = 64;
     int batch_mode = LBM_BATCH_STREAMS;  // mode of the class batches created from now on
+    std::map<int, std::pair<int, int>> class_kernel;  // class -> (variant, segment) set by the client
     cudaStream_t stream = nullptr;
     std::map<int, lbm_batch*> batches;
     // shared with clients
@@ -98,12 +99,19 @@ void admit(lbm_server* s) {
         if (!b) {
             rc = lbm_batch_create(j->req.desc.lattice, j->req.desc.geom.storage, j->req.desc.geom.collision, s->budget,
                                   &b);
-            int mode = LBM_BATCH_STREAMS;
+            int mode = LBM_BATCH_STREAMS, variant = -1, segment = 0;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 mode = s->batch_mode;
+                auto it = s->class_kernel.find(key);
+                if (it != s->class_kernel.end()) {
+                    variant = it->second.first;
+                    segment = it->second.second;
+                }
             }
             if (rc == LBM_OK && mode != LBM_BATCH_STREAMS) rc = lbm_batch_set_mode(b, mode);
+            if (rc == LBM_OK && variant >= 0) rc = lbm_batch_set_variant(b, variant);
+            if (rc == LBM_OK && segment > 0 && mode == LBM_BATCH_PERSISTENT) rc = lbm_batch_set_segment(b, segment);
             if (rc == LBM_OK) rc = lbm_batch_set_stream(b, s->stream);
         }
         if (rc == LBM_OK) rc = lbm_batch_add(b, &j->req.desc, &j->slot);
@@ -287,6 +295,18 @@ int lbm_server_set_batch_mode(lbm_server* s, int mode) {
     if (mode != LBM_BATCH_STREAMS && mode != LBM_BATCH_PERSISTENT) return set_error(LBM_EINVAL, "bad batch mode");
     std::lock_guard<std::mutex> lk(s->mu);
     s->batch_mode = mode;
+    return LBM_OK;
+}
+
+int lbm_server_set_class_kernel(lbm_server* s, int lattice, int storage, int collision, int variant, int segment) {
+    if (!s) return set_error(LBM_EINVAL, "null server");
+    if (variant < -1 || segment < 0) return set_error(LBM_EINVAL, "bad variant or segment");
+    lbm_instance_desc d{};
+    d.lattice = lattice;
+    d.geom.storage = storage;
+    d.geom.collision = collision;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->class_kernel[class_key(d)] = std::make_pair(variant, segment);
     return LBM_OK;
 }
 

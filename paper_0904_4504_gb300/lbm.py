@@ -78,6 +78,10 @@ class lbm_info_t(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class lbm_batch_tune_entry(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("segment", ctypes.c_int), ("us_per_step", ctypes.c_double)]
+
+
 class lbm_instance_desc(ctypes.Structure):
     _fields_ = [
         ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
@@ -200,12 +204,19 @@ def lib():
             "lbm_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
             "lbm_batch_set_segment": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(lbm_instance_desc), ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(lbm_batch_tune_entry), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+            "lbm_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(lbm_instance_desc), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(lbm_batch_tune_entry)]),
             "lbm_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(lbm_batch_info_t)]),
             "lbm_batch_set_stream": (ctypes.c_int, [_P, _P]),
             "lbm_batch_destroy": (None, [_P]),
             "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
             "lbm_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(lbm_request), ctypes.POINTER(ctypes.c_longlong)]),
             "lbm_server_set_batch_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+            "lbm_server_set_class_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                           ctypes.c_int]),
             "lbm_server_poll": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.POINTER(lbm_result)]),
             "lbm_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_double, ctypes.POINTER(lbm_result)]),
             "lbm_server_force_history": (ctypes.c_int, [_P, ctypes.c_longlong, _D, ctypes.c_size_t,
@@ -449,6 +460,23 @@ def lbm_batch_set_variant(batch: int, variant: int) -> None:
     _check(lib().lbm_batch_set_variant(batch, variant))
 
 
+def lbm_batch_tune(batch: int, descs, steps: int = 20) -> list:
+    """Time the batch's kernel candidates on clones of the instance descriptions (see lbm.h)."""
+    arr = (lbm_instance_desc * len(descs))(*descs)
+    out = (lbm_batch_tune_entry * 64)()
+    n = ctypes.c_int()
+    _check(lib().lbm_batch_tune(batch, arr, len(descs), steps, out, 64, ctypes.byref(n)))
+    return [{"variant": out[k].variant, "segment": out[k].segment, "us_per_step": out[k].us_per_step}
+            for k in range(n.value)]
+
+
+def lbm_batch_autotune(batch: int, descs, steps: int = 20) -> dict:
+    arr = (lbm_instance_desc * len(descs))(*descs)
+    best = lbm_batch_tune_entry()
+    _check(lib().lbm_batch_autotune(batch, arr, len(descs), steps, ctypes.byref(best)))
+    return {"variant": best.variant, "segment": best.segment, "us_per_step": best.us_per_step}
+
+
 def lbm_batch_set_segment(batch: int, tiles: int) -> None:
     _check(lib().lbm_batch_set_segment(batch, tiles))
 
@@ -491,6 +519,11 @@ def make_request(desc: lbm_instance_desc, skip_periods: float, perimeter: float 
 
 def lbm_server_set_batch_mode(server: int, mode: int) -> None:
     _check(lib().lbm_server_set_batch_mode(server, mode))
+
+
+def lbm_server_set_class_kernel(server: int, lattice: int, storage: int, collision: int, variant: int,
+                                segment: int = 0) -> None:
+    _check(lib().lbm_server_set_class_kernel(server, lattice, storage, collision, variant, segment))
 
 
 def lbm_server_submit(server: int, req: lbm_request) -> int:
