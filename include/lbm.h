@@ -328,9 +328,11 @@ int lbm_batch_set_mode(lbm_batch* batch, int mode);
  * numbers; -1, the default: for D2Q37 the staged variant 27 with 16-bit storage and variant 2 with
  * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An
  * instance whose layout or wall scheme the variant does not support falls back to the plain
- * kernel.  In the persistent mode (before the first lbm_batch_add) it picks the persistent
- * kernel's tiles: 27 staged 64 x 3, 0 or 2 plain 32 x 4, -1 the default of the storage type;
- * other numbers are LBM_EINVAL there.  LBM_EINVAL for a number below -1. */
+ * kernel.  In the persistent mode (before the first lbm_batch_add) it picks the tile code the
+ * persistent kernel runs: 27 staged 64 x 3 tiles, 28 staged 128 x 3 (D2Q37), 2 plain 32 x 4
+ * (D2Q37 FP32/16-bit), 0 plain 32 x 4 (the others), -1 the default of the class (27 with 16-bit
+ * storage, else 2 or 0); a number the class does not build is LBM_EINVAL there.  LBM_EINVAL for a
+ * number below -1. */
 int lbm_batch_set_variant(lbm_batch* batch, int variant);
 
 /* Tiles per work item of the persistent kernel (default 4): its items are segments of this many
@@ -351,8 +353,8 @@ int lbm_batch_info(lbm_batch* batch, lbm_batch_info_t* out);
  * since a kernel's speed alone and in a batch differ.  Each candidate runs a temporary batch of
  * clones of `descs` (as many as the batch's budget holds) in this batch's mode for 2 + steps batch
  * steps, the last `steps` timed.  Candidates: in the streams mode the step-kernel variants built for
- * the class (variant; segment 0); in the persistent mode its two tile paths (variant 27 staged,
- * 2 plain) times segment lengths 1, 2, 4, 8.  Needs device memory for the clones. */
+ * the class (variant; segment 0); in the persistent mode the tile codes it runs for the class
+ * (variants 27, 28, 2, 0) times segment lengths 1, 2, 4, 8.  Needs device memory for the clones. */
 typedef struct {
     int variant;               /* lbm_batch_set_variant number                                   */
     int segment;               /* persistent mode: tiles per work item (lbm_batch_set_segment)   */

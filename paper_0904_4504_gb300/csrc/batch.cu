@@ -67,7 +67,7 @@ struct lbm_batch {
     int* d_err = nullptr;
     long long wait_limit = kDefaultWaitLimit;
     bool dirty = true;
-    int path = -1;                  // persistent kernel: PB_STAGED or PB_PLAIN (-1: not chosen yet)
+    int pvariant = -1;              // persistent kernel: the variant whose tile code it runs (-1: not chosen)
     PbKernel kernel{};
     int max_blocks = 0;             // co-resident blocks of the whole GPU
     // graph of one launch (queue reset, kernel), re-parameterized for every run
@@ -249,11 +249,20 @@ int launch(lbm_batch* b, int grid, long long step0, int nsteps) {
     return LBM_OK;
 }
 
-// Choose the persistent kernel of the batch's class (16-bit storage: staged tiles; else plain).
-int choose_kernel(lbm_batch* b, int path) {
-    if (path < 0) path = (b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16) ? PB_STAGED : PB_PLAIN;
-    const PbKernel k = find_pbatch_kernel(b->Q, b->storage, b->collision, path);
-    if (!k.func) return set_error(LBM_EINVAL, "no persistent kernel of path %d for this lattice/storage/collision", path);
+// The persistent kernel's default variant for the batch's class: staged 64 x 3 tiles (27) with
+// 16-bit storage, plain 32 x 4 tiles otherwise (2 for D2Q37 FP32, else 0).
+int default_pvariant(const lbm_batch* b) {
+    if (b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16) return 27;
+    return (b->Q == 37 && b->storage != LBM_STORE_F64) ? 2 : 0;
+}
+
+// Choose the persistent kernel of the batch's class by variant (-1: the default).
+int choose_kernel(lbm_batch* b, int variant) {
+    if (variant < 0) variant = default_pvariant(b);
+    const PbKernel k = find_pbatch_kernel(b->Q, b->storage, b->collision, variant);
+    if (!k.func)
+        return set_error(LBM_EINVAL, "the persistent kernel runs no variant %d for this lattice/storage/collision",
+                         variant);
     if (k.smem > 0)
         BCUDA(cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem));
     int per_sm = 0, sms = 0;
@@ -261,7 +270,7 @@ int choose_kernel(lbm_batch* b, int path) {
     BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     if (per_sm < 1) return set_error(LBM_ECUDA, "the persistent kernel does not fit on an SM");
     b->kernel = k;
-    b->path = path;
+    b->pvariant = variant;
     b->bx = k.tile_x;
     b->by = k.tile_y;
     b->max_blocks = per_sm * sms;
@@ -356,11 +365,9 @@ int lbm_batch_add(lbm_batch* b, const lbm_instance_desc* d, int* slot) {
     // instance does not wait for a run of the batch that may be in flight
     const bool half = b->storage == LBM_STORE_BF16 || b->storage == LBM_STORE_F16;
     if (b->mode == LBM_BATCH_PERSISTENT) {
-        // the instance's tile shape is the persistent kernel's: staged 64 x 3 tiles (variant 27:
-        // its load boxes and tile slots) or plain 32 x 4 tiles
-        if (b->path == PB_STAGED) rc = lbm_set_variant(sim, 27);
-        else if (b->Q == 37 && b->storage != LBM_STORE_F64) rc = lbm_set_variant(sim, 2);
-        else rc = lbm_set_tile(sim, 32, 4);
+        // the instance's tile shape is the persistent kernel's: that of the variant whose tile code
+        // it runs (for staged tiles also the load boxes)
+        rc = b->pvariant ? lbm_set_variant(sim, b->pvariant) : lbm_set_tile(sim, 32, 4);
     } else {
         // default kernels, fastest measured in this mode: for D2Q37, the staged kernel with three
         // rows per thread (27) for 16-bit storage and the plain kernel with 7 resident blocks per SM
@@ -565,10 +572,10 @@ int lbm_batch_set_mode(lbm_batch* b, int mode) {
     for (const Slot& s : b->slots)
         if (slot_live(s)) return set_error(LBM_EINVAL, "set the mode before adding instances");
     if (mode == LBM_BATCH_PERSISTENT) {
-        // the persistent kernel: staged tiles for variant 27, plain tiles for 0 or 2, the class's
-        // default otherwise
-        const int path = b->variant == 27 ? PB_STAGED : (b->variant == 0 || b->variant == 2) ? PB_PLAIN : -1;
-        if ((rc = choose_kernel(b, path))) return rc;
+        // the persistent kernel of the variant set before, if it runs one; the class's default otherwise
+        const int v = (b->variant >= 0 && find_pbatch_kernel(b->Q, b->storage, b->collision, b->variant).func)
+                          ? b->variant : -1;
+        if ((rc = choose_kernel(b, v))) return rc;
     } else {
         b->bx = 32;
         b->by = 4;
@@ -595,10 +602,7 @@ int lbm_batch_set_variant(lbm_batch* b, int variant) {
     if (b->mode == LBM_BATCH_PERSISTENT) {
         for (const Slot& s : b->slots)
             if (slot_live(s)) return set_error(LBM_EINVAL, "set the persistent kernel before adding instances");
-        const int path = variant == 27 ? PB_STAGED : (variant == 0 || variant == 2) ? PB_PLAIN : -1;
-        if (variant >= 0 && path < 0)
-            return set_error(LBM_EINVAL, "the persistent kernel runs variant 27 (staged) or 0/2 (plain), not %d", variant);
-        if ((rc = choose_kernel(b, path))) return rc;
+        if ((rc = choose_kernel(b, variant))) return rc;
     }
     b->variant = variant;
     return LBM_OK;
@@ -616,8 +620,8 @@ int lbm_batch_tune(lbm_batch* b, const lbm_instance_desc* descs, int n, int step
     if (b->mode == LBM_BATCH_STREAMS) {
         for (int v : {0, 1, 2, 10, 20, 26, 27, 30}) cand.push_back(lbm_batch_tune_entry{v, 0, 0.0});
     } else {
-        for (int v : {27, 2})
-            if (find_pbatch_kernel(b->Q, b->storage, b->collision, v == 27 ? PB_STAGED : PB_PLAIN).func)
+        for (int v : {27, 28, 2, 0})
+            if (find_pbatch_kernel(b->Q, b->storage, b->collision, v).func)
                 for (int sg : {1, 2, 4, 8}) cand.push_back(lbm_batch_tune_entry{v, sg, 0.0});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -30,7 +30,7 @@ void tma_box_q9(int storage, int bx, int* bw, int* pad);
 // D2Q37 launch tables, one translation unit per storage type (step_q37_inst.cuh).
 #define LBM_Q37_DECLS(SFX)                                          \
     void* find_launcher_q37_##SFX(int coll);                        \
-    PbKernel find_pbatch_q37_##SFX(int coll, int path);             \
+    PbKernel find_pbatch_q37_##SFX(int coll, int variant);          \
     void* find_launcher_q37_##SFX##_ds(int coll);                   \
     void* find_occ_launcher_q37_##SFX(int coll, int variant);       \
     void* find_tma_launcher_q37_##SFX(int coll, int variant);       \
@@ -43,7 +43,7 @@ LBM_Q37_DECLS(f16)
 
 struct Q37Table {
     void* (*plain)(int coll);
-    PbKernel (*pbatch)(int coll, int path);
+    PbKernel (*pbatch)(int coll, int variant);
     void* (*plain_ds)(int coll);
     void* (*occ)(int coll, int variant);
     void* (*tma)(int coll, int variant);
@@ -83,6 +83,7 @@ static bool variant_tile(int variant, int* bx, int* by) {
         case 25: *bx = 128; *by = 2; return true;
         case 26:
         case 27: *bx = 64; *by = 3; return true;
+        case 28: *bx = 128; *by = 3; return true;
         case 20: *bx = 64; *by = 4; return true;
         case 30: *bx = 128; *by = 4; return true;
         case 21: *bx = 64; *by = 2; return true;
@@ -127,7 +128,7 @@ static int encode_map(CUtensorMap* map, void* base, int storage, int nx, int ny,
 
 void* find_launcher_q9(int storage, int coll);
 void* find_launcher_q9_ds(int storage, int coll);
-PbKernel find_pbatch_q9(int storage, int coll, int path);
+PbKernel find_pbatch_q9(int storage, int coll, int variant);
 
 static void* find_launcher(int Q, int storage, int coll) {
     if (Q == 9) return find_launcher_q9(storage, coll);
@@ -166,9 +167,9 @@ StepLaunchFn find_step_launcher(int Q, int storage, int coll, int wall) {
     else if (Q == 37 && q37_table(storage)) f = q37_table(storage)->plain_ds(coll);
     return reinterpret_cast<StepLaunchFn>(f);
 }
-PbKernel find_pbatch_kernel(int Q, int storage, int coll, int path) {
-    if (Q == 9) return find_pbatch_q9(storage, coll, path);
-    if (Q == 37 && q37_table(storage)) return q37_table(storage)->pbatch(coll, path);
+PbKernel find_pbatch_kernel(int Q, int storage, int coll, int variant) {
+    if (Q == 9) return find_pbatch_q9(storage, coll, variant);
+    if (Q == 37 && q37_table(storage)) return q37_table(storage)->pbatch(coll, variant);
     return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 

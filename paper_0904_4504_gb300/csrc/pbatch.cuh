@@ -25,7 +25,7 @@
 // thread per column, or plain tiles of 32 x 4 nodes with global loads), so every instance is
 // computed exactly as lbm_step computes it with the same tile shape.  The populations other blocks
 // of the launch wrote are read after an acquire of their row counters: by TMA (after a proxy
-// fence) or by loads through L2 (ld.global.cg), never from L1 or the read-only path.
+// fence) or by plain weak loads, never through the read-only path.
 #pragma once
 
 #include <cuda.h>
@@ -336,9 +336,10 @@ PbKernel pbatch_kernel_info() {
     return k;
 }
 
-// The persistent kernel of a (lattice, storage, collision) class, by path:
-// PB_STAGED = staged tiles of 64 x 3 nodes (64 threads, the 16-bit batch kernel),
-// PB_PLAIN = plain tiles of 32 x 4 nodes (128 threads); func is null if not built.
-PbKernel find_pbatch_kernel(int Q, int storage, int coll, int path);
+// The persistent kernel of a (lattice, storage, collision) class, by the variant whose tile code it
+// runs (lbm_set_variant numbers): 27 = staged 64 x 3 tiles, 28 = staged 128 x 3 tiles (D2Q37),
+// 2 = plain 32 x 4 tiles (D2Q37, 4- and 2-byte storage), 0 = plain 32 x 4 tiles (the others);
+// func is null if not built.
+PbKernel find_pbatch_kernel(int Q, int storage, int coll, int variant);
 
 }  // namespace lbm

@@ -131,17 +131,18 @@ __device__ __forceinline__ float kconst<float>(double, float f) { return f; }
 template <class ST> struct StoreT;
 // Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
 // elements) with one access; rnd(v) is v rounded to the storage type (what a store and a load give).
-// ldc loads through L2 only (ld.global.cg), never from L1 or the read-only path (ld.global.nc)
-// that the compiler may pick for a const __restrict__ pointer: the persistent batch kernel reads
-// populations that other blocks of the same launch wrote (made visible by an acquire), and an L1
-// line filled before that could still hold the old value.
+// ldc is a plain weak load (ld.global.ca), never the read-only path (ld.global.nc) that the
+// compiler may pick for a const __restrict__ pointer: the persistent batch kernel reads populations
+// that other blocks of the same launch wrote.  They are visible to weak loads that follow the
+// acquire of their producer's release (in the block, through the block barrier), which is what the
+// memory model guarantees; it guarantees nothing for the read-only path.
 template <> struct StoreT<double> {
     using CT = double;
     static __device__ __forceinline__ double rnd(double v) { return v; }
     static __device__ __forceinline__ double ld(const double* p) { return *p; }
     static __device__ __forceinline__ double ldc(const double* p) {
         double v;
-        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return v;
     }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
@@ -160,7 +161,7 @@ template <> struct StoreT<float> {
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ float ldc(const float* p) {
         float v;
-        asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
@@ -179,7 +180,7 @@ template <> struct StoreT<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ float ldc(const __nv_bfloat16* p) {
         unsigned short v;
-        asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+        asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __bfloat162float(__ushort_as_bfloat16(v));
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
@@ -198,7 +199,7 @@ template <> struct StoreT<__half> {
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ float ldc(const __half* p) {
         unsigned short v;
-        asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+        asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __half2float(__ushort_as_half(v));
     }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }

@@ -15,24 +15,28 @@ void* q37_plain(int coll) {
     return nullptr;
 }
 
-// The persistent batch kernel (pbatch.cuh): staged 64 x 3 tiles (16-bit storage: 11 blocks of 64
-// threads per SM, the shape of variant 27; FP32: 6, as shared memory allows) or plain 32 x 4 tiles
-// (6 blocks of 128 threads per SM, the register budget of variant 1; FP64: 3).
+// The persistent batch kernel (pbatch.cuh), by the variant whose tile code it runs: 27 = staged
+// 64 x 3 tiles (16-bit storage: 11 blocks of 64 threads per SM; FP32: 6, as shared memory allows),
+// 28 = staged 128 x 3 tiles (6 blocks of 128 threads), 2 = plain 32 x 4 tiles (6 blocks of 128
+// threads per SM, the register budget of variant 1), 0 = plain 32 x 4 tiles for FP64 (3 blocks).
 template <class ST, int COLL>
-PbKernel q37_pbatch_c(int path) {
+PbKernel q37_pbatch_c(int variant) {
     constexpr bool wide = sizeof(ST) == 8;
     if constexpr (!wide) {
-        if (path == PB_STAGED)
+        if (variant == 27)
             return pbatch_kernel_info<D2Q37, ST, COLL, PB_STAGED, 64, 3, sizeof(ST) == 2 ? 11 : 6>();
+        if (variant == 28) return pbatch_kernel_info<D2Q37, ST, COLL, PB_STAGED, 128, 3, sizeof(ST) == 2 ? 6 : 3>();
+        if (variant == 2) return pbatch_kernel_info<D2Q37, ST, COLL, PB_PLAIN, 32, 4, 6>();
+    } else {
+        if (variant == 0) return pbatch_kernel_info<D2Q37, ST, COLL, PB_PLAIN, 32, 4, 3>();
     }
-    if (path == PB_PLAIN) return pbatch_kernel_info<D2Q37, ST, COLL, PB_PLAIN, 32, 4, wide ? 3 : 6>();
     return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
 template <class ST>
-PbKernel q37_pbatch(int coll, int path) {
-    if (coll == COLL_REG) return q37_pbatch_c<ST, COLL_REG>(path);
-    if (coll == COLL_BGK) return q37_pbatch_c<ST, COLL_BGK>(path);
+PbKernel q37_pbatch(int coll, int variant) {
+    if (coll == COLL_REG) return q37_pbatch_c<ST, COLL_REG>(variant);
+    if (coll == COLL_BGK) return q37_pbatch_c<ST, COLL_BGK>(variant);
     return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
@@ -60,7 +64,8 @@ void* q37_occ_c(int variant) {
 // Staged steps (tiles in nodes): 10, 11, 12 = one node per thread on 32 x 4, 64 x 2, 64 x 4 tiles;
 // 13 = 64 x 2 with the outputs stored through TMA; 18, 23, 24, 25 = several nodes per thread, one
 // row apart: blocks of 64 x 1 (4 rows), 64 x 1 (2 rows), 64 x 1 (4 rows, 10 blocks per SM),
-// 128 x 1 (2 rows) threads; 26, 27 = 64 x 1 threads, 3 rows, at least 12 or 11 blocks per SM.
+// 128 x 1 (2 rows) threads; 26, 27 = 64 x 1 threads, 3 rows, at least 12 or 11 blocks per SM;
+// 28 = 128 x 1 threads, 3 rows, 6 blocks per SM.
 template <class ST, int COLL>
 void* q37_tma_c(int variant) {
     switch (variant) {
@@ -74,6 +79,7 @@ void* q37_tma_c(int variant) {
         case 25: return (void*)&launch_step_tman<D2Q37, ST, COLL, 128, 1, 2, 6>;
         case 26: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 3, 12>;
         case 27: return (void*)&launch_step_tman<D2Q37, ST, COLL, 64, 1, 3, 11>;
+        case 28: return (void*)&launch_step_tman<D2Q37, ST, COLL, 128, 1, 3, 6>;
         default: return nullptr;
     }
 }
@@ -103,7 +109,7 @@ void q37_box(int bx, int* bw, int* pad) {
 #define LBM_Q37_EXPORTS(SFX, ST, STAGED)                                                                 \
     namespace lbm {                                                                                      \
     void* find_launcher_q37_##SFX(int coll) { return q37_plain<ST>(coll); }                           \
-    PbKernel find_pbatch_q37_##SFX(int coll, int path) { return q37_pbatch<ST>(coll, path); }          \
+    PbKernel find_pbatch_q37_##SFX(int coll, int variant) { return q37_pbatch<ST>(coll, variant); }    \
     void* find_launcher_q37_##SFX##_ds(int coll) { return q37_plain_ds<ST>(coll); }                    \
     void* find_occ_launcher_q37_##SFX(int coll, int variant) {                                          \
         return STAGED ? q37_occ<ST>(coll, variant) : nullptr;                                            \

@@ -25,31 +25,32 @@ void* find_launcher_q9(int storage, int coll) {
 
 #undef LBM_CASE
 
-// The persistent batch kernel (pbatch.cuh): staged 64 x 3 tiles (16-bit, FP32) or plain 32 x 4 tiles.
+// The persistent batch kernel (pbatch.cuh), by the variant whose tile code it runs: 27 = staged
+// 64 x 3 tiles (16-bit storage, FP32), 0 = plain 32 x 4 tiles.
 template <class ST, int COLL>
-PbKernel q9_pbatch_c(int path) {
+PbKernel q9_pbatch_c(int variant) {
     constexpr bool wide = sizeof(ST) == 8;
     if constexpr (!wide) {
-        if (path == PB_STAGED)
+        if (variant == 27)
             return pbatch_kernel_info<D2Q9, ST, COLL, PB_STAGED, 64, 3, sizeof(ST) == 2 ? 16 : 12>();
     }
-    if (path == PB_PLAIN) return pbatch_kernel_info<D2Q9, ST, COLL, PB_PLAIN, 32, 4, wide ? 6 : 8>();
+    if (variant == 0) return pbatch_kernel_info<D2Q9, ST, COLL, PB_PLAIN, 32, 4, wide ? 6 : 8>();
     return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
 template <class ST>
-PbKernel q9_pbatch_s(int coll, int path) {
-    if (coll == COLL_REG) return q9_pbatch_c<ST, COLL_REG>(path);
-    if (coll == COLL_BGK) return q9_pbatch_c<ST, COLL_BGK>(path);
+PbKernel q9_pbatch_s(int coll, int variant) {
+    if (coll == COLL_REG) return q9_pbatch_c<ST, COLL_REG>(variant);
+    if (coll == COLL_BGK) return q9_pbatch_c<ST, COLL_BGK>(variant);
     return PbKernel{nullptr, dim3(), 0, 0, 0};
 }
 
-PbKernel find_pbatch_q9(int storage, int coll, int path) {
+PbKernel find_pbatch_q9(int storage, int coll, int variant) {
     switch (storage) {
-        case ST_F64: return q9_pbatch_s<double>(coll, path);
-        case ST_F32: return q9_pbatch_s<float>(coll, path);
-        case ST_BF16: return q9_pbatch_s<__nv_bfloat16>(coll, path);
-        case ST_F16: return q9_pbatch_s<__half>(coll, path);
+        case ST_F64: return q9_pbatch_s<double>(coll, variant);
+        case ST_F32: return q9_pbatch_s<float>(coll, variant);
+        case ST_BF16: return q9_pbatch_s<__nv_bfloat16>(coll, variant);
+        case ST_F16: return q9_pbatch_s<__half>(coll, variant);
         default: return PbKernel{nullptr, dim3(), 0, 0, 0};
     }
 }

@@ -212,7 +212,8 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
     configs = [("tile", (32, 8)), ("tile", (64, 4)), ("tile", (128, 1)), ("tile", (32, 16)),
                ("variant", 1), ("variant", 2), ("variant", 3), ("variant", 4), ("variant", 10), ("variant", 11),
                ("variant", 12), ("variant", 13),
-               ("variant", 18), ("variant", 23), ("variant", 24), ("variant", 25), ("variant", 26), ("variant", 27)]
+               ("variant", 18), ("variant", 23), ("variant", 24), ("variant", 25), ("variant", 26), ("variant", 27),
+               ("variant", 28)]
     for kind, arg in configs:
         geom = L.make_geometry(kind=L.LBM_GEOM_BEAM, lx=24, ly=19, drive=L.LBM_DRIVE_BODYFORCE, u0=1e-3, eq_order=4,
                                storage=storage)
@@ -238,7 +239,7 @@ def test_kernel_variants_and_tiles_do_not_change_results(storage):
         assert np.abs(F - outs[0][1]).max() <= Ftol, (kind, arg)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 10, 11, 12, 13, 18, 23, 24, 25, 26, 27])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 10, 11, 12, 13, 18, 23, 24, 25, 26, 27, 28])
 def test_parity_staged_variants(variant):
     """The occupancy-floor (1, 2) and TMA-staged kernels against the oracle on a grid with interior
     tiles, FP32."""
@@ -267,7 +268,7 @@ def test_parity_staged_variants(variant):
 # The multi-row staged kernels in 16-bit storage (the batch runs 27) against the oracle on 393 x 90:
 # staged interior tiles, an odd width (a ragged last tile on the plain path) and a 23-wide beam, so
 # that interior tiles hold solid and boundary nodes.
-STAGED16 = [18, 26, 27]
+STAGED16 = [18, 26, 27, 28]
 
 
 @pytest.mark.parametrize("st", [L.LBM_STORE_BF16, L.LBM_STORE_F16])
