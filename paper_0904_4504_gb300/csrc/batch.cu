@@ -618,7 +618,7 @@ int lbm_batch_tune(lbm_batch* b, const lbm_instance_desc* descs, int n, int step
     // (staged 27, plain 2) times the segment lengths
     std::vector<lbm_batch_tune_entry> cand;
     if (b->mode == LBM_BATCH_STREAMS) {
-        for (int v : {0, 1, 2, 10, 20, 26, 27, 30}) cand.push_back(lbm_batch_tune_entry{v, 0, 0.0});
+        for (int v : {0, 1, 2, 10, 20, 26, 27, 28, 30}) cand.push_back(lbm_batch_tune_entry{v, 0, 0.0});
     } else {
         for (int v : {27, 28, 2, 0})
             if (find_pbatch_kernel(b->Q, b->storage, b->collision, v).func)

@@ -24,7 +24,7 @@
 namespace lbm {
 
 void* find_tma_launcher_q9(int storage, int coll, int variant);
-void* find_q9v_launcher(int storage, int coll);
+void* find_q9v_launcher(int storage, int coll, int variant);
 void tma_box_q9(int storage, int bx, int* bw, int* pad);
 
 // D2Q37 launch tables, one translation unit per storage type (step_q37_inst.cuh).
@@ -877,7 +877,7 @@ int lbm_create(int lattice, int nx, int ny, double tau, double omega, const lbm_
     // 16-bit D2Q9 the four-nodes-per-thread kernel on 128 x 4 tiles (variant 30)
     if (!s->aa && g.wall_scheme == LBM_SCHEME_BOUNCEBACK) {
         if (lattice == LBM_D2Q9 && es == 2) {
-            StepLaunchFn f = reinterpret_cast<StepLaunchFn>(find_q9v_launcher(g.storage, g.collision));
+            StepLaunchFn f = reinterpret_cast<StepLaunchFn>(find_q9v_launcher(g.storage, g.collision, 30));
             if (f) {
                 s->launch = f;
                 s->variant = 30;
@@ -921,8 +921,8 @@ int lbm_set_variant(lbm_sim* s, int variant) {
     if (s->geom.wall_scheme != LBM_SCHEME_BOUNCEBACK)
         return set_error(LBM_EINVAL, "kernel variants are built for bounce-back walls only");
     if ((variant >= 1 && variant <= 4) || variant == 30) {
-        StepLaunchFn f = variant == 30 ? (s->Q == 9 ? reinterpret_cast<StepLaunchFn>(
-                                                          find_q9v_launcher(s->geom.storage, s->geom.collision))
+        StepLaunchFn f = variant >= 30 ? (s->Q == 9 ? reinterpret_cast<StepLaunchFn>(find_q9v_launcher(
+                                                          s->geom.storage, s->geom.collision, variant))
                                                     : nullptr)
                                        : find_occ_launcher(s->Q, s->geom.storage, s->geom.collision, variant);
         if (!f) return set_error(LBM_EINVAL, "variant %d is not built for this lattice/storage/collision", variant);

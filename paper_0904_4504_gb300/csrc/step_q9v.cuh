@@ -146,142 +146,175 @@ __device__ __forceinline__ void q9_collide2(const InstDev& P, float dv_f, const 
     }
 }
 
-template <class ST, int COLL, int MINB>
-__global__ void __launch_bounds__(128, MINB) step_kernel_q9v(const __grid_constant__ InstDev P) {
+// The source rows of one thread's four nodes: per direction the four stored values of its pulled
+// row (w0: elements 0, 1; w1: elements 2, 3) and the value shifted in by c_x (h(x0 - 1) for
+// c_x = +1, h(x0 + 4) for c_x = -1).
+struct Q9Row {
+    unsigned w0[9], w1[9];
+    unsigned short sh[9];
+};
+
+// Loads of the row y of a thread's nodes x0 .. x0 + 3 (warp-uniform y: the shuffles need the whole
+// warp; `any`: this thread owns a node inside the grid).
+template <class ST>
+__device__ __forceinline__ void q9v_load(const InstDev& P, int x0, int y, int lane, bool any, Q9Row& R) {
+    using L = D2Q9;
+    const ST* __restrict__ src = static_cast<const ST*>(P.src);
+    const unsigned plane = (unsigned)P.plane;
+    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    int ys[3];  // source row of c_y = -1, 0, +1
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int r = y - d;
+        r += r < 0 ? ny : 0;
+        r -= r >= ny ? ny : 0;
+        ys[d + 1] = r;
+    }
+    const int xl = x0 == 0 ? nx - 1 : x0 - 1;   // left neighbour column (periodic)
+    const int xr = x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4;
+    const bool edge_l = lane == 0 || x0 == 0;
+    const bool edge_r = lane == 31 || x0 + 4 >= nx;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = cx_of<L>(i), cy = cy_of<L>(i);
+        const unsigned rowoff = (unsigned)(i * plane + ys[cy + 1] * pitch);
+        uint2 v = make_uint2(0u, 0u);
+        if (any) v = *reinterpret_cast<const uint2*>(src + rowoff + x0);
+        R.w0[i] = v.x;
+        R.w1[i] = v.y;
+        if (cx == 1) {
+            const unsigned up = __shfl_up_sync(0xffffffffu, v.y, 1);
+            unsigned short s = (unsigned short)(up >> 16);
+            if (edge_l && any) s = *reinterpret_cast<const unsigned short*>(src + rowoff + xl);
+            R.sh[i] = s;
+        } else if (cx == -1) {
+            const unsigned dn = __shfl_down_sync(0xffffffffu, v.x, 1);
+            unsigned short s = (unsigned short)(dn & 0xffffu);
+            if (edge_r && any && x0 + 4 <= nx) s = *reinterpret_cast<const unsigned short*>(src + rowoff + xr);
+            R.sh[i] = s;
+        } else {
+            R.sh[i] = 0;
+        }
+    }
+}
+
+// Collision and store of a thread's four nodes of row y from their loaded source rows.
+template <class ST, int COLL>
+__device__ __forceinline__ void q9v_compute(const InstDev& P, int x0, int y, unsigned cls4, const Q9Row& R, double& Fx,
+                                            double& Fy) {
     using L = D2Q9;
     using H = Half16<ST>;
     constexpr int Q = 9;
+    const ST* __restrict__ src = static_cast<const ST*>(P.src);
+    const unsigned plane = (unsigned)P.plane;
+    const int nx = P.nx, pitch = P.pitch;
+    ST* __restrict__ dst = static_cast<ST*>(P.dst) + (size_t)y * pitch + x0;
+    unsigned o0[Q], o1[Q];
+    if (x0 + 4 <= nx) {
+        // value of direction i pulled to node j (0..3) of this thread
+        auto pulled = [&](int i, int j) -> float {
+            const int cx = cx_of<L>(i);
+            const int e = j - cx;  // element of the loaded vector, -1 or 4: the shifted-in one
+            if (e < 0 || e > 3) return H::lo((unsigned)R.sh[i]);
+            return e == 0 ? H::lo(R.w0[i]) : e == 1 ? H::hi(R.w0[i]) : e == 2 ? H::lo(R.w1[i]) : H::hi(R.w1[i]);
+        };
+        const bool off = P.stream_off != 0;
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            const int ca = (cls4 >> (16 * pr)) & 0xff, cb = (cls4 >> (16 * pr + 8)) & 0xff;
+            if (ca == NODE_SOLID && cb == NODE_SOLID) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) (pr == 0 ? o0 : o1)[i] = 0u;
+                continue;
+            }
+            // pulled populations of the pair's two nodes; the stream offset and the wall rule
+            // (Eq. 12, with the momentum handed to the body) per node, as in prepare
+            float ha[Q], hb[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                ha[i] = pulled(i, 2 * pr);
+                hb[i] = pulled(i, 2 * pr + 1);
+                if (off && COLL == COLL_BGK) {
+                    ha[i] += off_l<L>(P, i);
+                    hb[i] += off_l<L>(P, i);
+                }
+            }
+            const int idx = y * pitch + x0 + 2 * pr;
+            if (ca == NODE_BOUNDARY) bb_fixup<L, ST, COLL, OWN_OPP>(P, src, idx, P.dv, ha, Fx, Fy);
+            if (cb == NODE_BOUNDARY) bb_fixup<L, ST, COLL, OWN_OPP>(P, src, idx + 1, P.dv, hb, Fx, Fy);
+            F2 Hp[Q], Op[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Hp[i] = f2(ha[i], hb[i]);
+            q9_collide2<COLL>(P, P.dv_f, Hp, Op);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float va, vb;
+                f2_split(Op[i], va, vb);
+                (pr == 0 ? o0 : o1)[i] = H::pack(ca == NODE_SOLID ? 0.f : va, cb == NODE_SOLID ? 0.f : vb);
+            }
+        }
+    } else {
+        // the last vector of a row that ends inside it: per-node gathers with the periodic wrap
+#pragma unroll 1
+        for (int pr = 0; pr < 2; ++pr) {
+            float out[2][Q];
+            for (int jj = 0; jj < 2; ++jj) {
+                const int j = 2 * pr + jj;
+                const int c = (cls4 >> (8 * j)) & 0xff;
+                if (x0 + j >= nx || c == NODE_SOLID) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) out[jj][i] = 0.f;
+                    continue;
+                }
+                float h[Q];
+                gather_global<L, ST>(P, src, x0 + j, y, h);
+                Coef<float> C;
+                prepare<L, ST, COLL>(P, P.src, x0 + j, y, c, P.dv, P.dv_f, h, Fx, Fy, C);
+                emit_outputs<L, ST, COLL>(C, h, [&](int i, float v) { out[jj][i] = v; });
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) (pr == 0 ? o0 : o1)[i] = H::pack(out[0][i], out[1][i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *reinterpret_cast<uint2*>(dst + (size_t)i * plane) = make_uint2(o0[i], o1[i]);
+}
+
+// NR rows per thread, 4 apart (tiles of 128 x 4 NR nodes): the loads of all NR rows are issued
+// before the first row is computed, so that more bytes are in flight per thread.
+template <class ST, int COLL, int NR, int MINB>
+__global__ void __launch_bounds__(128, MINB) step_kernel_q9v(const __grid_constant__ InstDev P) {
     const int t = blockIdx.x;
     const int slot = P.tile_slot[t];  // geometry (host-written): read before the wait
     const int lane = threadIdx.x;
     const int x0 = (t % P.ntx) * 128 + 4 * lane;
-    const int y = (t / P.ntx) * 4 + threadIdx.y;
-    const bool row = y < P.ny;                 // warp-uniform
-    const bool any = row && x0 < P.nx;         // this thread owns at least one node
-    unsigned cls4 = 0x01010101u;               // NODE_SOLID x 4
-    if (any) cls4 = *reinterpret_cast<const unsigned*>(P.cls + (size_t)y * P.pitch + x0);
+    const int y0 = (t / P.ntx) * (4 * NR) + threadIdx.y;
+    unsigned cls4[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int y = y0 + 4 * r;
+        cls4[r] = 0x01010101u;  // NODE_SOLID x 4
+        if (y < P.ny && x0 < P.nx) cls4[r] = *reinterpret_cast<const unsigned*>(P.cls + (size_t)y * P.pitch + x0);
+    }
     pdl_wait_then_release();
     double Fx = 0.0, Fy = 0.0;
-    if (row) {
-        const ST* __restrict__ src = static_cast<const ST*>(P.src);
-        const unsigned plane = (unsigned)P.plane;
-        const int nx = P.nx, ny = P.ny, pitch = P.pitch;
-        int ys[3];  // source row of c_y = -1, 0, +1
+    Q9Row R[NR];
 #pragma unroll
-        for (int d = -1; d <= 1; ++d) {
-            int r = y - d;
-            r += r < 0 ? ny : 0;
-            r -= r >= ny ? ny : 0;
-            ys[d + 1] = r;
-        }
-        const int xl = x0 == 0 ? nx - 1 : x0 - 1;   // left neighbour column (periodic)
-        const int xr = x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4;
-        const bool edge_l = lane == 0 || x0 == 0;
-        const bool edge_r = lane == 31 || x0 + 4 >= nx;
-        // the four stored values of every direction's source row, and the shifted-in neighbours
-        unsigned w0[Q], w1[Q];
-        unsigned short sh[Q];  // value shifted in: h(x0 - 1) for c_x = +1, h(x0 + 4) for c_x = -1
+    for (int r = 0; r < NR; ++r) {
+        const int y = y0 + 4 * r;
+        if (y < P.ny) q9v_load<ST>(P, x0, y, lane, x0 < P.nx, R[r]);  // warp-uniform row test
+    }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = cx_of<L>(i), cy = cy_of<L>(i);
-            const unsigned rowoff = (unsigned)(i * plane + ys[cy + 1] * pitch);
-            uint2 v = make_uint2(0u, 0u);
-            if (any) v = *reinterpret_cast<const uint2*>(src + rowoff + x0);
-            w0[i] = v.x;
-            w1[i] = v.y;
-            if (cx == 1) {
-                const unsigned up = __shfl_up_sync(0xffffffffu, v.y, 1);
-                unsigned short s = (unsigned short)(up >> 16);
-                if (edge_l && any) s = *reinterpret_cast<const unsigned short*>(src + rowoff + xl);
-                sh[i] = s;
-            } else if (cx == -1) {
-                const unsigned dn = __shfl_down_sync(0xffffffffu, v.x, 1);
-                unsigned short s = (unsigned short)(dn & 0xffffu);
-                if (edge_r && any && x0 + 4 <= nx) s = *reinterpret_cast<const unsigned short*>(src + rowoff + xr);
-                sh[i] = s;
-            } else {
-                sh[i] = 0;
-            }
-        }
-        if (any) {
-            ST* __restrict__ dst = static_cast<ST*>(P.dst) + (size_t)y * pitch + x0;
-            unsigned o0[Q], o1[Q];
-            if (x0 + 4 <= nx) {
-                // value of direction i pulled to node j (0..3) of this thread
-                auto pulled = [&](int i, int j) -> float {
-                    const int cx = cx_of<L>(i);
-                    const int e = j - cx;  // element of the loaded vector, -1 or 4: the shifted-in one
-                    if (e < 0 || e > 3) return H::lo((unsigned)sh[i]);
-                    return e == 0 ? H::lo(w0[i]) : e == 1 ? H::hi(w0[i]) : e == 2 ? H::lo(w1[i]) : H::hi(w1[i]);
-                };
-                const bool off = P.stream_off != 0;
-#pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int ca = (cls4 >> (16 * pr)) & 0xff, cb = (cls4 >> (16 * pr + 8)) & 0xff;
-                    if (ca == NODE_SOLID && cb == NODE_SOLID) {
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) (pr == 0 ? o0 : o1)[i] = 0u;
-                        continue;
-                    }
-                    // pulled populations of the pair's two nodes; the stream offset and the wall
-                    // rule (Eq. 12, with the momentum handed to the body) per node, as in prepare
-                    float ha[Q], hb[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        ha[i] = pulled(i, 2 * pr);
-                        hb[i] = pulled(i, 2 * pr + 1);
-                        if (off && COLL == COLL_BGK) {
-                            ha[i] += off_l<L>(P, i);
-                            hb[i] += off_l<L>(P, i);
-                        }
-                    }
-                    const int idx = y * pitch + x0 + 2 * pr;
-                    if (ca == NODE_BOUNDARY) bb_fixup<L, ST, COLL, OWN_OPP>(P, src, idx, P.dv, ha, Fx, Fy);
-                    if (cb == NODE_BOUNDARY) bb_fixup<L, ST, COLL, OWN_OPP>(P, src, idx + 1, P.dv, hb, Fx, Fy);
-                    F2 Hp[Q], Op[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) Hp[i] = f2(ha[i], hb[i]);
-                    q9_collide2<COLL>(P, P.dv_f, Hp, Op);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        float va, vb;
-                        f2_split(Op[i], va, vb);
-                        (pr == 0 ? o0 : o1)[i] = H::pack(ca == NODE_SOLID ? 0.f : va, cb == NODE_SOLID ? 0.f : vb);
-                    }
-                }
-            } else {
-                // the last vector of a row that ends inside it: per-node gathers with the periodic wrap
-#pragma unroll 1
-                for (int pr = 0; pr < 2; ++pr) {
-                    float out[2][Q];
-                    for (int jj = 0; jj < 2; ++jj) {
-                        const int j = 2 * pr + jj;
-                        const int c = (cls4 >> (8 * j)) & 0xff;
-                        if (x0 + j >= nx || c == NODE_SOLID) {
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) out[jj][i] = 0.f;
-                            continue;
-                        }
-                        float h[Q];
-                        gather_global<L, ST>(P, src, x0 + j, y, h);
-                        Coef<float> C;
-                        prepare<L, ST, COLL>(P, P.src, x0 + j, y, c, P.dv, P.dv_f, h, Fx, Fy, C);
-                        emit_outputs<L, ST, COLL>(C, h, [&](int i, float v) { out[jj][i] = v; });
-                    }
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) (pr == 0 ? o0 : o1)[i] = H::pack(out[0][i], out[1][i]);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < Q; ++i) *reinterpret_cast<uint2*>(dst + (size_t)i * plane) = make_uint2(o0[i], o1[i]);
-        }
+    for (int r = 0; r < NR; ++r) {
+        const int y = y0 + 4 * r;
+        if (y < P.ny && x0 < P.nx) q9v_compute<ST, COLL>(P, x0, y, cls4[r], R[r], Fx, Fy);
     }
     tile_epilogue(P, slot, P.force_out, Fx, Fy);
 }
 
-template <class ST, int COLL, int MINB>
+template <class ST, int COLL, int NR, int MINB>
 cudaError_t launch_step_q9v(const InstDev& P, dim3, cudaStream_t stream) {
-    return launch_pdl(step_kernel_q9v<ST, COLL, MINB>, dim3(P.ntiles), dim3(32, 4), 0, stream, P);
+    return launch_pdl(step_kernel_q9v<ST, COLL, NR, MINB>, dim3(P.ntiles), dim3(32, 4), 0, stream, P);
 }
 
 }  // namespace lbm
