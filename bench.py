@@ -12,6 +12,8 @@ Workloads (synthetic, shaped like the paper's cases):
             batch modes), the 2048^2 precision study, and the served FP16 request stream (saturated,
             at 70 % load, and its D2Q9 requests alone) with p50/p99 latency.
   plate9    D2Q9 plain BGK, FP64: the 4 x 256 oscillating plate (latency-bound correctness case).
+  plate9-2048[-f16|-bf16]  a D2Q9 regularized plate in a 2048^2 box at tau*omega = 0.3 (the largest
+            D2Q9 request shape of the served stream; profiling).
   beam2048-<f32|f16|bf16|f64>  D2Q37-H4 beam in a 2048^2 box, tau*omega = 0.1, 1, 10.
   serve[-f16]  the serving loop: the first --requests requests of the seeded request stream (plate
             or beam, AR 0.25..4, tau*omega 1e-3..1e3, sides 128..2048, 10..50 periods, D2Q9 or
@@ -117,6 +119,11 @@ def workload_list(name):
         return [I.beam_d2q37_h4(1.0, storage=st)]
     if name == "plate9":
         return [I.plate_d2q9_fp64()]
+    if name.startswith("plate9-2048"):
+        # the largest D2Q9 request shape of the served stream: a 2048^2 plate, regularized, moving wall
+        st = STORE[name.split("-")[2]] if name.count("-") == 2 else STORE["f32"]
+        return [I.Workload("plate-d2q9-2048", 9, 2048, 2048, 0.3, I.PLATE, drive=I.DRIVE_WALL, u0=1e-3, eq_order=2,
+                           collision=I.REG, storage=st, periods=10.0)]
     if name.startswith("beam2048-"):
         st = STORE[name.split("-")[1]]
         return [I.beam_d2q37_h4(to, n=2048, storage=st) for to in I.PRECISION_TAU_OMEGAS]
