@@ -1,6 +1,6 @@
 // server.cu -- continuous-batching request loop (lbm_server_* in include/lbm.h).
 //
-// A worker thread owns one batch per (lattice, storage, collision) class, all on one stream.
+// A worker thread owns one batch per (lattice, storage, collision) class, each on its own stream.
 // Each round it enqueues a run of K steps (lbm_batch_run) for every class with running instances,
 // then -- while the GPU works -- admits waiting requests in arrival order as long as their device
 // footprint fits the budget (they join the next round), waits for the round, and retires the
@@ -49,7 +49,6 @@ struct lbm_server {
     int steps_per_round = 64;
     int batch_mode = LBM_BATCH_STREAMS;  // mode of the class batches created from now on
     std::map<int, std::pair<int, int>> class_kernel;  // class -> (variant, segment) set by the client
-    cudaStream_t stream = nullptr;
     std::map<int, lbm_batch*> batches;
     // shared with clients
     std::mutex mu;
@@ -112,7 +111,8 @@ void admit(lbm_server* s) {
             if (rc == LBM_OK && mode != LBM_BATCH_STREAMS) rc = lbm_batch_set_mode(b, mode);
             if (rc == LBM_OK && variant >= 0) rc = lbm_batch_set_variant(b, variant);
             if (rc == LBM_OK && segment > 0 && mode == LBM_BATCH_PERSISTENT) rc = lbm_batch_set_segment(b, segment);
-            if (rc == LBM_OK) rc = lbm_batch_set_stream(b, s->stream);
+            // each class batch keeps its own stream, so that the rounds of different classes
+            // (D2Q9 and D2Q37, FP32 and FP16) run at the same time on the GPU
         }
         if (rc == LBM_OK) rc = lbm_batch_add(b, &j->req.desc, &j->slot);
         if (rc != LBM_OK) {
@@ -250,10 +250,6 @@ int lbm_server_create(size_t device_budget_bytes, int steps_per_round, lbm_serve
     const size_t margin = (size_t)2 << 30;
     s->budget = device_budget_bytes ? device_budget_bytes : (free_b > margin ? free_b - margin : free_b / 2);
     s->steps_per_round = steps_per_round;
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete s;
-        return set_error(LBM_ECUDA, "stream creation");
-    }
     s->t0 = Clock::now();
     s->worker = std::thread(worker_main, s);
     *out = s;
@@ -391,7 +387,6 @@ void lbm_server_destroy(lbm_server* s) {
     if (s->worker.joinable()) s->worker.join();
     for (auto& kv : s->batches) lbm_batch_destroy(kv.second);
     for (auto& kv : s->jobs) delete kv.second;
-    if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
 

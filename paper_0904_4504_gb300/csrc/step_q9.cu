@@ -56,16 +56,19 @@ PbKernel find_pbatch_q9(int storage, int coll, int variant) {
 }
 
 // The four-nodes-per-thread kernel of 16-bit storage (variant 30, 128 x 4 tiles; step_q9v.cuh).
-// The regularized collision fits 80 registers (6 blocks per SM); plain BGK keeps the nine pulled
-// values live for its outputs and takes 5.  (Two rows per thread with both rows' loads issued
-// first, 128 x 8 tiles, measured 0.54-0.64 against 0.56-0.63 on the same box: not built.)
+// The kernel is latency bound, so the occupancy floor is set above what the registers alone
+// give: the regularized collision at 8 blocks per SM (64 registers, 8 B spilled; measured 0.62 /
+// 0.73 of the copy peak at 2048^2 / 4096^2 against 0.56 / 0.63 at its unspilled 6 blocks, 0.61 /
+// 0.72 at 9 and 0.53 / 0.62 at 10), plain BGK at 7 (0.57 against 0.55 at 6 and 8).  (Two rows per
+// thread with both rows' loads issued first, 128 x 8 tiles, measured 0.54-0.64 against 0.56-0.63
+// on the same box: not built.)
 void* find_q9v_launcher(int storage, int coll, int variant) {
     if (variant != 30) return nullptr;
     switch (storage * 2 + coll) {
-        case ST_BF16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_BGK, 1, 5>;
-        case ST_BF16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_REG, 1, 6>;
-        case ST_F16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__half, COLL_BGK, 1, 5>;
-        case ST_F16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__half, COLL_REG, 1, 6>;
+        case ST_BF16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_BGK, 1, 7>;
+        case ST_BF16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__nv_bfloat16, COLL_REG, 1, 8>;
+        case ST_F16 * 2 + COLL_BGK: return (void*)&launch_step_q9v<__half, COLL_BGK, 1, 7>;
+        case ST_F16 * 2 + COLL_REG: return (void*)&launch_step_q9v<__half, COLL_REG, 1, 8>;
         default: return nullptr;
     }
 }
