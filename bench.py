@@ -358,7 +358,7 @@ def run_batch(args, sub=False):
                        "batch_mode": "persistent" if info["mode"] == 1 else "streams",
                        "graph": bool(info["uses_graph"]), "grid_blocks": info["max_blocks"], "layout": args.layout,
                        "kernel_variant": used[0] if len(used) == 1 else used,
-                       "segment_tiles": args.batch_segment or "library default",
+                       "strip_tile_rows": args.batch_segment or "library default",
                        "autotuned": tuned},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
@@ -658,7 +658,7 @@ def run_ours(args):
             extras["batched_mixed_precision_persistent"] = dict(
                 keep(p16, "value", "unit", "steps", "ms_per_step", "roofline", "clocks", "gpu_launches", "config"),
                 workload="sweep64-f16 in the persistent mode: one launch per 64 steps of the persistent kernel "
-                         "(staged 64 x 3 tiles) through a CUDA graph",
+                         "(staged 64 x 3 tiles, work items of one tile column x 8 tile rows) through a CUDA graph",
                 speedup_vs_plain_fp32=round(p16["value"] / value, 4))
             if prec is not None:
                 extras["precision_study"] = prec
@@ -800,7 +800,7 @@ def main():
                     help="sweep64/serve: choose the batch kernels with the batch autotuner (JSON cache in the temp "
                          "dir) before the timed region (1) or use the library's defaults (0)")
     ap.add_argument("--batch-segment", type=int, default=0,
-                    help="sweep64, persistent mode: tiles per work item (0: the library's default)")
+                    help="sweep64, persistent mode: tile rows per work item (strip; 0: the library's default)")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the step kernel")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end C-ABI run (profiling runs)")

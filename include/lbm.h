@@ -326,7 +326,8 @@ int lbm_batch_set_mode(lbm_batch* batch, int mode);
 
 /* Step kernel of the instances added after this call, in the streams mode (lbm_set_variant
  * numbers; -1, the default: for D2Q37 the staged variant 27 with 16-bit storage and variant 2 with
- * FP32; for 16-bit D2Q9 the staged variant 10; else the plain kernel on 32 x 4 tiles).  An
+ * FP32; for 16-bit D2Q9 the four-nodes-per-thread variant 30; else the plain kernel on 32 x 4
+ * tiles).  An
  * instance whose layout or wall scheme the variant does not support falls back to the plain
  * kernel.  In the persistent mode (before the first lbm_batch_add) it picks the tile code the
  * persistent kernel runs: 27 staged 64 x 3 tiles, 28 staged 128 x 3 (D2Q37), 2 plain 32 x 4
@@ -335,11 +336,12 @@ int lbm_batch_set_mode(lbm_batch* batch, int mode);
  * number below -1. */
 int lbm_batch_set_variant(lbm_batch* batch, int variant);
 
-/* Tiles per work item of the persistent kernel (default 4): its items are segments of this many
- * consecutive tiles of one tile row, taken in row order, so that neighbouring tiles run at about the
- * same time and share their halo reads in L2; longer segments spread the per-item cost (a queue
- * atomic, the dependency check) over more tiles.  Fixed once the batch has run in the persistent
- * mode (the row counters count segments).  LBM_EINVAL outside 1..1024 or after that. */
+/* Tile rows per work item of the persistent kernel (default 8): its items are strips, one tile
+ * column of a band of this many tile rows; the strips of a band are taken one after another, so
+ * they walk down their columns side by side and horizontally neighbouring tiles share their halo
+ * reads in L2.  Longer strips spread the per-item cost (a queue atomic, the dependency check) over
+ * more tiles; shorter ones give more items to balance.  Fixed once the batch has run in the
+ * persistent mode (the band counters count strips).  LBM_EINVAL outside 1..1024 or after that. */
 int lbm_batch_set_segment(lbm_batch* batch, int tiles);
 
 /* Clock cycles a block of the persistent kernel waits for another tile's progress before giving
@@ -354,10 +356,10 @@ int lbm_batch_info(lbm_batch* batch, lbm_batch_info_t* out);
  * clones of `descs` (as many as the batch's budget holds) in this batch's mode for 2 + steps batch
  * steps, the last `steps` timed.  Candidates: in the streams mode the step-kernel variants built for
  * the class (variant; segment 0); in the persistent mode the tile codes it runs for the class
- * (variants 27, 28, 2, 0) times segment lengths 1, 2, 4, 8.  Needs device memory for the clones. */
+ * (variants 27, 28, 2, 0) times strip lengths 4, 8, 12.  Needs device memory for the clones. */
 typedef struct {
     int variant;               /* lbm_batch_set_variant number                                   */
-    int segment;               /* persistent mode: tiles per work item (lbm_batch_set_segment)   */
+    int segment;               /* persistent mode: tile rows per strip (lbm_batch_set_segment)   */
     double us_per_step;        /* time of one batch step of the clones                           */
 } lbm_batch_tune_entry;
 

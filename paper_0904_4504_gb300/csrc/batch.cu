@@ -29,9 +29,8 @@ struct Slot {
     lbm_sim* sim = nullptr;
     long long start = 0;      // batch step of the instance's step 0
     long long nsteps = 0;
-    // persistent mode: one allocation holding the per-step constants [nsteps], the tile-row
-    // segment counters [nty], the force ring [kRing][nslots], its tickets [kRing] and finish marks
-    // [kRing]
+    // persistent mode: one allocation holding the per-step constants [nsteps], the band counters
+    // [<= nty], the force ring [kRing][nslots], its tickets [kRing] and finish marks [kRing]
     unsigned char* d_pb = nullptr;
     size_t off_done = 0, off_ring = 0, off_tickets = 0, off_fin = 0;
     size_t bytes = 0;
@@ -58,11 +57,11 @@ struct lbm_batch {
     // device arrays of the launch
     PInst* d_insts = nullptr;
     size_t insts_cap = 0;
-    int4* d_segs = nullptr;         // (instance, tile row, first tile, end tile) of the running instances
+    int4* d_segs = nullptr;         // (instance, band, tile column, 0) of the running instances
     size_t segs_cap = 0;
     int nsegs = 0;
-    int seg_tiles = 4;              // tiles per work item of the persistent kernel
-    int pinned_seg = 0;             // segment length fixed by the seg_tiles in use at the first run
+    int seg_tiles = 8;              // tile rows per work item (strip) of the persistent kernel
+    int pinned_seg = 0;             // strip length fixed by the seg_tiles in use at the first run
     unsigned long long* d_queue = nullptr;  // work-item counter of the persistent kernel
     int* d_err = nullptr;
     long long wait_limit = kDefaultWaitLimit;
@@ -148,7 +147,7 @@ size_t footprint(const HostLattice& H, int nx, int ny, int storage, int layout, 
            hist * sizeof(double2) + pb_layout(nsteps, (int)tiles, (int)tiles, nullptr) + 4096;
 }
 
-// Rebuild the per-instance launch table and the row-segment list of the unfinished instances.
+// Rebuild the per-instance launch table and the strip list of the unfinished instances.
 int rebuild(lbm_batch* b) {
     std::vector<PInst> insts(std::max<size_t>(1, b->slots.size()));
     std::vector<int4> segs;
@@ -174,10 +173,12 @@ int rebuild(lbm_batch* b) {
         I.by = v.by;
         I.nty = (v.ny + v.by - 1) / v.by;
         const int ntx = v.inst.ntx, S = b->seg_tiles;
-        I.nseg = (ntx + S - 1) / S;
+        I.band = S;
+        I.nseg = ntx;
         if (!slot_running(b, s)) continue;
-        for (int r = 0; r < I.nty; ++r)
-            for (int t0 = 0; t0 < ntx; t0 += S) segs.push_back(make_int4((int)k, r, t0, std::min(t0 + S, ntx)));
+        // the columns of a band follow each other, so that they run side by side
+        for (int band = 0; band * S < I.nty; ++band)
+            for (int tx = 0; tx < ntx; ++tx) segs.push_back(make_int4((int)k, band, tx, 0));
     }
     if (insts.size() > b->insts_cap) {
         cudaFree(b->d_insts);
@@ -587,10 +588,10 @@ int lbm_batch_set_mode(lbm_batch* b, int mode) {
 int lbm_batch_set_segment(lbm_batch* b, int tiles) {
     int rc = check_batch(b);
     if (rc) return rc;
-    if (tiles < 1 || tiles > 1024) return set_error(LBM_EINVAL, "segment of %d tiles: need 1..1024", tiles);
-    // the row counters count segments, so the length is fixed once the persistent kernel has run
+    if (tiles < 1 || tiles > 1024) return set_error(LBM_EINVAL, "strip of %d tile rows: need 1..1024", tiles);
+    // the band counters count strips, so the length is fixed once the persistent kernel has run
     if (b->pinned_seg && tiles != b->pinned_seg)
-        return set_error(LBM_EINVAL, "the segment length is fixed after the first persistent run");
+        return set_error(LBM_EINVAL, "the strip length is fixed after the first persistent run");
     b->seg_tiles = tiles;
     return LBM_OK;
 }
@@ -615,14 +616,14 @@ int lbm_batch_tune(lbm_batch* b, const lbm_instance_desc* descs, int n, int step
     if (!descs || n < 1 || steps < 1 || !n_out || (cap > 0 && !out))
         return set_error(LBM_EINVAL, "need instance descriptions, steps >= 1 and an output");
     // candidates: streams mode, the step kernels of the class; persistent mode, its tile paths
-    // (staged 27, plain 2) times the segment lengths
+    // (staged 27 and 28, plain 2 and 0) times the strip lengths
     std::vector<lbm_batch_tune_entry> cand;
     if (b->mode == LBM_BATCH_STREAMS) {
         for (int v : {0, 1, 2, 10, 20, 26, 27, 28, 30}) cand.push_back(lbm_batch_tune_entry{v, 0, 0.0});
     } else {
         for (int v : {27, 28, 2, 0})
             if (find_pbatch_kernel(b->Q, b->storage, b->collision, v).func)
-                for (int sg : {1, 2, 4, 8}) cand.push_back(lbm_batch_tune_entry{v, sg, 0.0});
+                for (int sg : {4, 8, 12}) cand.push_back(lbm_batch_tune_entry{v, sg, 0.0});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

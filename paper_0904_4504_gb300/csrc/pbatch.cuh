@@ -1,17 +1,21 @@
 // pbatch.cuh -- the persistent batched step: one launch advances many lattice instances of uneven
 // sizes by K time steps, with no grid-wide barrier.
 //
-// Work items are (batch step k, row segment) pairs in step-major order; a row segment is a run of
-// a few consecutive tiles of one tile row of one instance, and the segments of a row follow each
-// other in the list, so that neighbouring tiles run at about the same time on different blocks and
-// share their halo reads in L2.  Blocks take items from a global counter (one atomic per item,
-// fetched one item ahead).  A segment of local step n + 1 waits only for the tile rows of its own
-// instance within the lattice reach of its row to have finished step n: that one condition covers
-// both the populations it reads (written at step n) and the ones it overwrites (read at step n by
-// those neighbours).  Each row counts its finished segments in a per-instance array (row r has
-// finished step n when its count reaches (n + 1) x segments per row).  Because items are taken in
-// step-major order, every item a segment waits for was taken earlier by a running block, so the
-// wait always ends; no co-residency of the grid is needed.
+// Work items are (batch step k, strip) pairs in step-major order.  A strip is one tile column of a
+// band of S tile rows of one instance; the strips of a band follow each other in the list.  Blocks
+// take items from a global counter (one atomic per item, taken when the block is ready to start
+// it), so the strips of a band start together and walk down their columns side by side:
+// horizontally neighbouring tiles, whose staged boxes overlap by the lattice reach (and by the
+// 32-byte sectors around it), are read at about the same time and share those reads in L2.  (An
+// item index fetched one item ahead decorrelates the start of neighbouring strips by up to one
+// item's duration, long enough for the shared sectors to leave L2: 1.4x the algorithmic DRAM reads
+// against 1.1x.)  A strip of local step n + 1 waits only for the bands of its own instance within
+// the lattice reach of its band to have finished step n: that one condition covers both the
+// populations it reads (written at step n) and the ones it overwrites (read at step n by those
+// neighbours).  Each band counts its finished strips in a per-instance array (band b has finished
+// step n when its count reaches (n + 1) x tile columns).  Because items are taken in step-major
+// order, every item a strip waits for was taken earlier by a running block, so the wait always
+// ends; no co-residency of the grid is needed.
 //
 // The force of a step is reduced as in the single-instance kernels (per-tile FP64 slot, fixed-
 // order sum by the last slot tile), into a ring of force slots indexed by n mod kRing, so that
@@ -24,7 +28,7 @@
 // The tile code is that of the single-instance kernels (staged TMA tiles of BX x NR nodes, one
 // thread per column, or plain tiles of 32 x 4 nodes with global loads), so every instance is
 // computed exactly as lbm_step computes it with the same tile shape.  The populations other blocks
-// of the launch wrote are read after an acquire of their row counters: by TMA (after a proxy
+// of the launch wrote are read after an acquire of their band counters: by TMA (after a proxy
 // fence) or by plain weak loads, never through the read-only path.
 #pragma once
 
@@ -57,7 +61,7 @@ struct alignas(64) PInst {
     const void* buf[2];        // population buffers; local step n reads buf[n & 1]
     const StepConst* steps;    // [nsteps]
     double2* history;          // [nsteps] force of each local step
-    int* done;                 // [nty] segments of each tile row completed, over all steps
+    int* done;                 // [bands] strips of each band completed, over all steps
     double2* ring;             // [kRing][nslots] force partials
     unsigned int* tickets;     // [kRing] slot tiles of the ring entry's step that have finished
     int* fin;                  // [kRing] 1 + the last step whose force left the entry
@@ -65,7 +69,8 @@ struct alignas(64) PInst {
     long long nsteps;          // local steps to run
     int nty;                   // tiles along y
     int bx, by;                // tile shape in nodes
-    int nseg;                  // segments per tile row
+    int band;                  // tile rows per band (the tiles of one strip)
+    int nseg;                  // strips per band (tile columns)
 };
 
 enum PbPath { PB_STAGED = 0, PB_PLAIN = 1 };
@@ -80,43 +85,43 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Tile rows of an instance (rows of by >= R nodes along a periodic axis of ny nodes, the last one
-// possibly shorter) that hold a node within reach R of row ty, each listed once: at most four (R
-// nodes on either side span at most two rows, the short last one and its neighbour).
-__device__ __forceinline__ int halo_rows(int ty, int by, int ny, int R, int (&out)[4]) {
-    const int a = ty * by - R;                    // first node of the halo (>= -R)
-    const int b = min(ty * by + by, ny) - 1 + R;  // last node (< ny + by + R)
+// Bands of an instance (bands of h >= R nodes along a periodic axis of ny nodes, the last one
+// possibly shorter) that hold a node within reach R of band b, each listed once: at most four (R
+// nodes on either side span at most two bands, the short last one and its neighbour).
+__device__ __forceinline__ int halo_bands(int band, int h, int ny, int R, int (&out)[4]) {
+    const int first = band * h - R;                   // first node of the halo (>= -R)
+    const int last = min(band * h + h, ny) - 1 + R;   // last node (< ny + h + R)
     int k = 0;
-    for (int c = a; c <= b && k < 4;) {
+    for (int c = first; c <= last && k < 4;) {
         int cw = c % ny;
         if (cw < 0) cw += ny;
-        const int tt = cw / by;
+        const int bb = cw / h;
         bool seen = false;
-        for (int j = 0; j < k; ++j) seen = seen || out[j] == tt;
-        if (!seen) out[k++] = tt;
-        c += min((tt + 1) * by, ny) - cw;  // first node of the next row of tiles
+        for (int j = 0; j < k; ++j) seen = seen || out[j] == bb;
+        if (!seen) out[k++] = bb;
+        c += min((bb + 1) * h, ny) - cw;  // first node of the next band
     }
     return k;
 }
 
-// Warp 0: wait until every tile row within reach of row ty of the instance has completed local
-// step n - 1, i.e. counted n x nseg segments (lanes 0-3, one row each; only for n >= 1), and until
-// the sum of the force of step n - kRing has left ring entry n mod kRing (lane 4; instances with
-// body links, n >= kRing).
+// Warp 0: wait until every band within reach of band b of the instance has completed local step
+// n - 1, i.e. counted n x nseg strips (lanes 0-3, one band each; only for n >= 1), and until the
+// sum of the force of step n - kRing has left ring entry n mod kRing (lane 4; instances with body
+// links, n >= kRing).
 // Returns false (in every lane) if a wait ran out.
 template <class L>
-__device__ __forceinline__ bool wait_item(const PInst& I, int ty, long long n, long long limit) {
-    int rows[4];
-    const int nr = n > 0 ? halo_rows(ty, I.by, I.base.ny, L::R, rows) : 0;
+__device__ __forceinline__ bool wait_item(const PInst& I, int band, long long n, long long limit) {
+    int bands[4];
+    const int nb = n > 0 ? halo_bands(band, I.band * I.by, I.base.ny, L::R, bands) : 0;
     const int lane = threadIdx.x & 31;
     const int* p = nullptr;
     int need = 0;
-    if (lane < nr) {
-        int r = rows[0];
+    if (lane < nb) {
+        int b = bands[0];
 #pragma unroll
         for (int j = 1; j < 4; ++j)
-            if (lane == j) r = rows[j];
-        p = I.done + r;
+            if (lane == j) b = bands[j];
+        p = I.done + b;
         need = (int)n * I.nseg;
     } else if (lane == 4 && I.base.nslots > 0 && n >= kRing) {
         p = I.fin + (int)(n % kRing);
@@ -140,8 +145,8 @@ __device__ __forceinline__ bool wait_item(const PInst& I, int ty, long long n, l
 // Launch parameters of the persistent kernel.
 struct PbArgs {
     const PInst* insts;
-    const int4* segs;             // (instance, tile row, first tile, end tile) of every row segment
-    int nsegs;                    // row segments per batch step
+    const int4* segs;             // (instance, band, tile column, 0) of every strip
+    int nsegs;                    // strips per batch step
     int nsteps;                   // batch steps of this launch
     long long step0;              // batch step of the launch's first step
     unsigned long long* queue;    // item counter (monotonic over launches)
@@ -184,30 +189,29 @@ __global__ void __launch_bounds__(PbShape<L, ST, COLL, PATH, BX, NR, MINB>::THRE
             mbar_init(&bar, 1);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        s_next = atomicAdd(A.queue, 1ull) - A.base;
         s_fail = 0;
         s_inst = -1;
         s_n = -1;
     }
     uint32_t parity = 0;
     while (true) {
-        __syncthreads();  // s_next is written; the previous item is finished
+        __syncthreads();  // the previous item is finished and every thread has read s_next
+        if (tid == 0) s_next = atomicAdd(A.queue, 1ull) - A.base;
+        __syncthreads();
         const unsigned long long w = s_next;
-        __syncthreads();  // every thread has read s_next
         if (w >= total) break;
-        if (tid == 0) s_next = atomicAdd(A.queue, 1ull) - A.base;  // the next item, fetched ahead
         const int k = (int)(w / (unsigned)A.nsegs);
         const int4 it = A.segs[w - (unsigned long long)k * (unsigned)A.nsegs];
         const PInst& I = A.insts[it.x];
         const long long n = A.step0 + k - I.start;
         if (n < 0 || n >= I.nsteps) continue;  // block-uniform: the instance does not run this step
-        const int ty = it.y;
+        const int band = it.y, tx = it.z;
         const int ring = (int)(n % kRing);
         const bool fresh = it.x != s_inst || n != s_n;  // P holds another instance or step
         // dependencies (warp 0, wait_item); the other warps meanwhile copy the instance's constants
         // into shared memory
         if (tid < 32) {
-            const bool ok = wait_item<L>(I, ty, n, A.limit);
+            const bool ok = wait_item<L>(I, band, n, A.limit);
             if (!ok && tid == 0) {
                 atomicOr(A.err, 8);
                 s_fail = 1;
@@ -246,7 +250,8 @@ __global__ void __launch_bounds__(PbShape<L, ST, COLL, PATH, BX, NR, MINB>::THRE
         if (PATH == PB_STAGED && tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();
         const int ntx = P.ntx;
-        for (int tx = it.z; tx < it.w; ++tx) {
+        const int ty0 = band * I.band, ty1 = min(ty0 + I.band, I.nty);
+        for (int ty = ty0; ty < ty1; ++ty) {
             const int t = ty * ntx + tx;
             const int slot = P.tile_slot[t];
             double Fx = 0.0, Fy = 0.0;
@@ -305,10 +310,10 @@ __global__ void __launch_bounds__(PbShape<L, ST, COLL, PATH, BX, NR, MINB>::THRE
             }
             if (PATH == PB_STAGED) __syncthreads();  // the stage is free for the next tile
         }
-        __syncthreads();  // every store of the segment issued
+        __syncthreads();  // every store of the strip issued
         if (tid == 0) {
             __threadfence();
-            atomicAdd(A.insts[it.x].done + ty, 1);
+            atomicAdd(A.insts[it.x].done + band, 1);
         }
     }
 }

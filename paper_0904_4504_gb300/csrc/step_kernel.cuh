@@ -131,6 +131,9 @@ __device__ __forceinline__ float kconst<float>(double, float f) { return f; }
 template <class ST> struct StoreT;
 // Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
 // elements) with one access; rnd(v) is v rounded to the storage type (what a store and a load give).
+// The 16-bit stores are streaming stores (st.global.cs): the next step reads them back long after
+// they have left L2, and marking them first to evict keeps the staged loads' shared halo sectors
+// in L2 longer.
 // ldc is a plain weak load (ld.global.ca), never the read-only path (ld.global.nc) that the
 // compiler may pick for a const __restrict__ pointer: the persistent batch kernel reads populations
 // that other blocks of the same launch wrote.  They are visible to weak loads that follow the
@@ -183,7 +186,9 @@ template <> struct StoreT<__nv_bfloat16> {
         asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __bfloat162float(__ushort_as_bfloat16(v));
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+        asm("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__bfloat16_as_ushort(__float2bfloat16_rn(v))));
+    }
     static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
         const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
         a = v.x;
@@ -202,7 +207,9 @@ template <> struct StoreT<__half> {
         asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __half2float(__ushort_as_half(v));
     }
-    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st(__half* p, float v) {
+        asm("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__half_as_ushort(__float2half_rn(v))));
+    }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
         const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
         a = v.x;
