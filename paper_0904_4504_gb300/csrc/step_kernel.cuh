@@ -131,9 +131,10 @@ __device__ __forceinline__ float kconst<float>(double, float f) { return f; }
 template <class ST> struct StoreT;
 // Loads and stores of the storage type; ld2/st2 move two neighbouring values (p aligned to two
 // elements) with one access; rnd(v) is v rounded to the storage type (what a store and a load give).
-// The 16-bit stores are streaming stores (st.global.cs): the next step reads them back long after
-// they have left L2, and marking them first to evict keeps the staged loads' shared halo sectors
-// in L2 longer.
+// st stores through a generic pointer (global or shared memory); stg stores to global memory only,
+// for 16-bit storage as a streaming store (st.global.cs): the next step reads the populations back
+// long after they have left L2, and marking them first to evict keeps the staged loads' shared halo
+// sectors in L2 longer.
 // ldc is a plain weak load (ld.global.ca), never the read-only path (ld.global.nc) that the
 // compiler may pick for a const __restrict__ pointer: the persistent batch kernel reads populations
 // that other blocks of the same launch wrote.  They are visible to weak loads that follow the
@@ -149,6 +150,7 @@ template <> struct StoreT<double> {
         return v;
     }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+    static __device__ __forceinline__ void stg(double* p, double v) { *p = v; }
     static __device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
         const double2 v = *reinterpret_cast<const double2*>(p);
         a = v.x;
@@ -168,6 +170,7 @@ template <> struct StoreT<float> {
         return v;
     }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void stg(float* p, float v) { *p = v; }
     static __device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
         const float2 v = *reinterpret_cast<const float2*>(p);
         a = v.x;
@@ -186,7 +189,8 @@ template <> struct StoreT<__nv_bfloat16> {
         asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __bfloat162float(__ushort_as_bfloat16(v));
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void stg(__nv_bfloat16* p, float v) {
         asm("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__bfloat16_as_ushort(__float2bfloat16_rn(v))));
     }
     static __device__ __forceinline__ void ld2(const __nv_bfloat16* p, float& a, float& b) {
@@ -207,7 +211,8 @@ template <> struct StoreT<__half> {
         asm volatile("ld.global.ca.u16 %0, [%1];" : "=h"(v) : "l"(p));
         return __half2float(__ushort_as_half(v));
     }
-    static __device__ __forceinline__ void st(__half* p, float v) {
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void stg(__half* p, float v) {
         asm("st.global.cs.b16 [%0], %1;" ::"l"(p), "h"(__half_as_ushort(__float2half_rn(v))));
     }
     static __device__ __forceinline__ void ld2(const __half* p, float& a, float& b) {
@@ -706,7 +711,7 @@ __device__ __forceinline__ void collide_store(const InstDev& P, const void* src_
     ST* __restrict__ dst = static_cast<ST*>(dst_v) + (y * P.pitch + x);
     const unsigned plane = (unsigned)P.plane;
     collide_emit<L, ST, COLL, WALL, COH>(P, src_v, x, y, cls, dv, dv_f, h, Fx, Fy,
-                                         [&](int i, T v) { S::st(dst + (unsigned long long)plane * (unsigned)i, v); });
+                                         [&](int i, T v) { S::stg(dst + (unsigned long long)plane * (unsigned)i, v); });
 }
 
 // Advection + wall + collision of the fluid node (x, y), sources from global memory.  WALL selects
