@@ -79,7 +79,11 @@ def kernel_source_hash():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the step kernels, from one
 # ncu capture each, with the digest of the sources they were captured from: once any source
 # changes, the entry no longer applies and the line reports traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("beam1024", 1): (263803648, "7754fcba7ecae327"),          # 156.4 MB read + 107.4 MB written
+    ("beam1024x1-f16", 26): (109410560, "7754fcba7ecae327"),   # 78.8 + 30.6 MB
+    ("beam1024x1-f16", 27): (109337088, "7754fcba7ecae327"),   # 78.8 + 30.5 MB
+}
 
 
 def traffic_for(workload, variant):
@@ -91,7 +95,11 @@ def traffic_for(workload, variant):
 # kernel, from the same kind of capture and with the same digest rule: with 16-bit storage the step
 # is bound by instruction issue, so the batched line also reports the issue rate against the SMs'
 # issue peak.
-INST_PER_NODE = {}
+INST_PER_NODE = {
+    ("beam1024", 1): (739.3, "7754fcba7ecae327"),              # 24,202,187 warp instructions, 1,047,552 fluid nodes
+    ("beam1024x1-f16", 26): (770.8, "7754fcba7ecae327"),       # 25,232,720
+    ("beam1024x1-f16", 27): (763.4, "7754fcba7ecae327"),       # 24,990,376
+}
 
 
 def inst_per_node(workload, variant):
@@ -363,8 +371,8 @@ def run_batch(args, sub=False):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": args.traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": "pbatch_kernel (persistent; per-row step counters, no grid barrier; one CUDA "
-                                   "graph launch per run)" if info["mode"] == 1 else
+                         "kernel": "pbatch_kernel (persistent; strips of tiles as work items, per-band step "
+                                   "counters, no grid barrier; one CUDA graph launch per run)" if info["mode"] == 1 else
                                    "step kernels of every instance on parallel streams",
                          "bytes_per_batch_step": bytes_step},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": launches, "cpu_baseline": None,
