@@ -108,6 +108,37 @@ def test_batch_equals_standalone_bitwise(mode, Q, st):
         L.lbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("strip", [1, 3, 64])
+@pytest.mark.parametrize("Q,st", [(37, L.LBM_STORE_F16), (37, L.LBM_STORE_F32), (9, L.LBM_STORE_F16)],
+                         ids=["q37-f16", "q37-f32", "q9-f16"])
+def test_persistent_strip_lengths_bitwise(Q, st, strip):
+    """The persistent kernel's work items are strips of `strip` tile rows: one tile row per strip,
+    a ragged last band, and strips longer than every instance (a single band, which is its own
+    neighbour across the periodic seam) all give the standalone results bit for bit.  The mix adds
+    the smallest grid a lattice allows (2R + 1 rows), whose bands of one tile row are shorter than
+    the reach on the last row."""
+    R = 3 if Q == 37 else 1
+    mix = MIX + [(40, 2 * R + 1, 0.8, 0.05, 19, dict(kind=L.LBM_GEOM_NONE))]
+    descs = [_desc(Q, nx, ny, tau, om, n, storage=st, **kw) for nx, ny, tau, om, n, kw in mix]
+    b = L.lbm_batch_create(Q, st, L.LBM_COLL_REGULARIZED)
+    try:
+        L.lbm_batch_set_mode(b, L.LBM_BATCH_PERSISTENT)
+        L.lbm_batch_set_segment(b, strip)
+        slots = [L.lbm_batch_add(b, d) for d in descs]
+        for k in (7, 2, 33):
+            L.lbm_batch_run(b, k)
+        L.lbm_batch_synchronize(b)
+        for d, s in zip(descs, slots):
+            sim = L.lbm_batch_instance(b, s)
+            g_a, F_a = _alone(d, L.LBM_BATCH_PERSISTENT)
+            assert (L.lbm_get_state(sim) == g_a).all(), (d.nx, d.ny)
+            assert (L.lbm_force_history(sim) == F_a).all(), (d.nx, d.ny)
+        with pytest.raises(L.LbmError):
+            L.lbm_batch_set_segment(b, strip + 1)  # fixed once the persistent kernel has run
+    finally:
+        L.lbm_batch_destroy(b)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_instances_joining_and_leaving_mid_run(mode):
     """An instance added after others ran, and another removed while others continue, do not change
