@@ -419,13 +419,14 @@ def run_serve(args, sub=False):
     else:
         arrivals = np.array([a for a, _ in reqs]) - reqs[0][0]
     srv = L.lbm_server_create(int(args.serve_budget_gb * 1e9), args.chunk)
+    L.lbm_server_set_batch_mode(srv, args.batch_mode)
     tuned = None
     if args.batch_autotune:
         # each request class's kernel, chosen by the batch autotuner on a sample of the class's
         # requests before the first submit (outside the timed region)
         from paper_0904_4504_gb300 import autotune as A
         t0 = time.perf_counter()
-        ch = A.tune_server(srv, [rq for _, rq in reqs], tune_cache_path(), steps=4, sample=8)
+        ch = A.tune_server(srv, [rq for _, rq in reqs], tune_cache_path(), steps=4, sample=8, mode=args.batch_mode)
         tuned = {f"Q{k[0]}-st{k[1]}-coll{k[2]}": v for k, v in ch.items()}
         tuned["tune_s"] = round(time.perf_counter() - t0, 2)
     ids = []
@@ -802,7 +803,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="beam1024: skip the batched and serving parts")
     ap.add_argument("--no-precision", action="store_true", help="beam1024: skip the 2048^2 precision study")
     ap.add_argument("--instances", type=int, default=0, help="sweep64: use only the first N instances (profiling)")
-    ap.add_argument("--batch-mode", type=int, default=0, help="sweep64: 0 parallel streams, 1 persistent cooperative")
+    ap.add_argument("--batch-mode", type=int, default=0,
+                    help="sweep64 and serve: 0 parallel streams, 1 the persistent kernel")
     ap.add_argument("--batch-variant", type=int, default=None, help="sweep64: step kernel of the streams mode")
     ap.add_argument("--batch-autotune", type=int, default=1,
                     help="sweep64/serve: choose the batch kernels with the batch autotuner (JSON cache in the temp "
