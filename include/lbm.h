@@ -251,10 +251,11 @@ int lbm_params_from_tau_omega(int lattice, double tau_omega, double delta_min, i
  * collision; each has its own grid, geometry, tau, omega, drive and length in steps (the tau*omega
  * and aspect-ratio sweep of Sec. 6).  In the persistent mode a run of K steps is one launch of a
  * persistent kernel, replayed through a CUDA graph (built once per grid size): its blocks take
- * (step, tile) items of every running instance from a queue in step order, and a tile waits only
- * for the tiles of its own instance within the lattice reach of it to have finished the previous
- * step -- there is no grid-wide barrier, and steps of different instances (and of distant tiles of
- * one instance) overlap.  Each wait is bounded (about 2 s by default); a wait that runs out sets
+ * (step, strip) items of every running instance from a queue in step order (a strip: one tile
+ * column of a band of tile rows, lbm_batch_set_segment), and a strip waits only for the bands of
+ * its own instance within the lattice reach of its band to have finished the previous step --
+ * there is no grid-wide barrier, and steps of different instances (and of distant bands of one
+ * instance) overlap.  Each wait is bounded (about 2 s by default); a wait that runs out sets
  * an error flag, the kernel returns, and lbm_batch_synchronize reports LBM_ETIMEOUT.  In both modes
  * every instance's arithmetic is that of lbm_step on the same instance with the same tile shape.
  * ---------------------------------------------------------------------------------------------- */
@@ -265,7 +266,7 @@ typedef struct lbm_batch lbm_batch; /* opaque; owned by the library */
  *                         fastest variant for the storage type) on one of several parallel
  *                         streams, so that instances of different sizes overlap (the default);
  *   LBM_BATCH_PERSISTENT  one launch per run of the persistent kernel over all instances' tiles
- *                         for K steps (per-tile step counters, no grid barrier), replayed through
+ *                         for K steps (per-band step counters, no grid barrier), replayed through
  *                         a CUDA graph: staged 64 x 3 tiles (the shape of variant 27) with 16-bit
  *                         storage, plain 32 x 4 tiles otherwise (lbm_batch_set_variant). */
 enum { LBM_BATCH_STREAMS = 0, LBM_BATCH_PERSISTENT = 1 };
