@@ -80,9 +80,9 @@ def kernel_source_hash():
 # ncu capture each, with the digest of the sources they were captured from: once any source
 # changes, the entry no longer applies and the line reports traffic null.
 TRAFFIC = {
-    ("beam1024", 1): (263803648, "7754fcba7ecae327"),          # 156.4 MB read + 107.4 MB written
-    ("beam1024x1-f16", 26): (109410560, "7754fcba7ecae327"),   # 78.8 + 30.6 MB
-    ("beam1024x1-f16", 27): (109337088, "7754fcba7ecae327"),   # 78.8 + 30.5 MB
+    ("beam1024", 1): (263564288, "6cb49ca6ec672d3b"),          # 156.4 MB read + 107.2 MB written
+    ("beam1024x1-f16", 26): (109641984, "6cb49ca6ec672d3b"),   # 78.8 + 30.8 MB
+    ("beam1024x1-f16", 27): (109117184, "6cb49ca6ec672d3b"),   # 78.8 + 30.3 MB
 }
 
 
@@ -96,9 +96,9 @@ def traffic_for(workload, variant):
 # is bound by instruction issue, so the batched line also reports the issue rate against the SMs'
 # issue peak.
 INST_PER_NODE = {
-    ("beam1024", 1): (739.3, "7754fcba7ecae327"),              # 24,202,187 warp instructions, 1,047,552 fluid nodes
-    ("beam1024x1-f16", 26): (770.8, "7754fcba7ecae327"),       # 25,232,720
-    ("beam1024x1-f16", 27): (763.4, "7754fcba7ecae327"),       # 24,990,376
+    ("beam1024", 1): (739.3, "6cb49ca6ec672d3b"),              # 24,202,187 warp instructions, 1,047,552 fluid nodes
+    ("beam1024x1-f16", 26): (770.8, "6cb49ca6ec672d3b"),       # 25,232,720
+    ("beam1024x1-f16", 27): (763.4, "6cb49ca6ec672d3b"),       # 24,990,376
 }
 
 
